@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark: events/s from linear-index EER to COM-DPC + SSB phase images.
+
+Workload: 1024x1024 scan, 576x576 detector binned 6x to 96x96 and cropped to
+the bright-field disk (553 pixels), 50 e-/frame (about 5.2e7 uint32 events,
+uint64 CSR offsets), seeded synthetic data.  One step = the whole hot path:
+eer_load_csr (validate + PACBED totals) -> com_dpc (COM sums + Fourier
+integrated DPC) -> ssb_accumulate (bin/crop/densify + scan DFT -> G) ->
+ssb_reconstruct (trotter + aberration phase + inverse transform + variance).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s to COM+SSB phase"
+UNIT = "events/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=5)
+    ap.add_argument("--refocus-steps", type=int, default=220)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# --------------------------------------------------------------- oracle arm --
+def oracle_pipeline(idx, off, geom):
+    """The FP64 oracle's whole path: COM + iDPC + densify + G + SSB phase."""
+    import oracle as orc
+    W, H = geom["det_w"], geom["det_h"]
+    sx, sy, n = orc.com_sums(idx, off, W, H)
+    cx, cy = orc.pacbed_centre(sx, sy, n)
+    ox, oy = orc.com_maps(sx, sy, n, cx, cy)
+    orc.idpc(ox, oy, geom)
+    counts = orc.densify(idx, off, geom)
+    G = orc.g_function(counts, geom)
+    return orc.ssb_phase(G, geom, (0.0, 0.0, 0.0, 0.0, 0.0), "none")
+
+
+def oracle_sample(scan: int, device: str):
+    import synth
+    w = synth.workload(5, scan_ny=scan, scan_nx=scan)
+    d = synth.generate(w, device)
+    idx, off = d.numpy()
+    return w, synth.geometry(w), idx, off
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def time_oracle(scan: int, device: str, reps: int = 1):
+    w, geom, idx, off = oracle_sample(scan, device)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle_pipeline(idx, off, geom)
+        ts.append(time.perf_counter() - t0)
+    return len(idx), ts, w
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    scan = 128
+    w, geom, idx, off = oracle_sample(scan, dev)
+    for _ in range(args.warmup):
+        oracle_pipeline(idx, off, geom)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_pipeline(idx, off, geom)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    v = len(idx) / t
+    cores = cpu_threads()
+    sample = (f"{scan}x{scan} scan of the same geometry and dose ({len(idx)} events, "
+              f"{scan * scan} frames) per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "scan": [scan, scan], "events_per_step": len(idx)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "affinity_cores": len(os.sched_getaffinity(0))},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm --
+STAGE_BYTES_DOC = {
+    "validate": "4 B/event + 8 B/frame",
+    "com": "4 B/event + 8 B/frame in; 40 B/frame out",
+    "dpc": "8 B/frame in + 4 B/frame out",
+    "scatter": "4 B/event + 8 B/frame in; 2 B x P_pad per frame out",
+    "dft_x": "2 B x P_pad per frame in; 8 B x P_pad x (Nx/2+1)/Nx per frame out",
+    "dft_y": "8 B x P_pad x (Nx/2+1)/Nx per frame in and out",
+    "trotter": "8 B per (pixel, K) pair of the trotter sets + 8 B per stored bin out",
+    "image": "8 B per stored bin in (x2) + 4 B/frame out",
+}
+
+
+def stage_bytes(C, F, P_pad, Ny, nkx, sigma_k):
+    half = Ny * nkx
+    return {
+        "validate": 4 * C + 8 * (F + 1),
+        "com": 4 * C + 8 * (F + 1) + 40 * F,
+        "dpc": 12 * F,
+        "scatter": 4 * C + 8 * (F + 1) + 2 * P_pad * F,
+        "dft_x": 2 * P_pad * F + 8 * P_pad * half,
+        "dft_y": 16 * P_pad * half,
+        "trotter": 8 * sigma_k + 8 * half,
+        "image": 16 * half + 4 * F,
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2104_06336_gb300 as P
+    import synth
+
+    P.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.workload, seed=synth.workload(args.workload).seed + 1000 * rank)
+    geom = synth.geometry(w)
+    d = synth.generate(w, dev)
+    idx, off = d.idx.contiguous(), d.off.contiguous()
+    C, F = idx.numel(), w.n_frames
+    rec = P.Reconstructor(geom, device=dev)
+    Ny, nkx, P_pad = w.scan_ny, rec.info["nkx"], rec.info["P_pad"]
+    theta = torch.zeros(5, dtype=torch.float64, device=dev)
+    sums = torch.empty(3, F, dtype=torch.int64, device=dev)
+    com = torch.empty(2, F, dtype=torch.float32, device=dev)
+    dpc = torch.empty(Ny, w.scan_nx, dtype=torch.float32, device=dev)
+    phase = torch.empty(1, Ny, w.scan_nx, dtype=torch.float32, device=dev)
+    var = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def step(ix, of):
+        rec.totals.zero_()
+        P.eer_load_csr(rec.plan, ix, of, totals=rec.totals, status=rec.status)
+        P.com_dpc(rec.plan, ix, of, sums, com, dpc, totals=rec.totals, scratch=rec.scratch,
+                  status=rec.status)
+        P.ssb_accumulate(rec.plan, ix, of, 0, rec.counts, rec.G, True, status=rec.status)
+        P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var, status=rec.status)
+
+    nst = len(P._lib.STAGES)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nst)] for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        step(idx, off)
+    torch.cuda.synchronize()
+    rec.check()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = P.eer4d_launch_count()
+    with ClockSampler(local_rank) as clk:
+        t_start.record()
+        for k in range(args.steps):
+            P.eer4d_set_stage_events(rec.plan, [e[0] for e in ev[k]], [e[1] for e in ev[k]])
+            step(idx, off)
+        t_stop.record()
+        torch.cuda.synchronize()
+    launches = P.eer4d_launch_count() - l0
+    P.eer4d_set_stage_events(rec.plan)
+    if world > 1:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_stop) / args.steps
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = world * C / (ms * 1e-3)
+    stage_ms = {n: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                for i, n in enumerate(P._lib.STAGES)}
+    rec.check()
+
+    # algorithmic bytes of each stage; sigma_k = sum over bins of |K(K)|
+    cnt = rec.trotter_counts(0.0)
+    sigma_k = int(cnt.sum().item())
+    sb = stage_bytes(C, F, P_pad, Ny, nkx, sigma_k)
+    hbm, hsrc = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    ach = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get(dom)
+        except Exception:
+            traffic = None
+    stages = {n: {"ms": round(stage_ms[n], 4), "bytes": sb[n],
+                  "GB_s": round(sb[n] / (stage_ms[n] * 1e-3) / 1e9, 1) if stage_ms[n] > 0 else None,
+                  "frac": round(sb[n] / (stage_ms[n] * 1e-3) / 1e9 / hbm, 3) if stage_ms[n] > 0 else None}
+              for n in P._lib.STAGES}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "scan": [w.scan_ny, w.scan_nx], "detector": [w.det_h, w.det_w],
+                   "bin": w.bin, "P": rec.info["P"], "events_per_gpu": C, "e_per_frame": w.e_per_frame,
+                   "precision": "FP32 FFT", "norm": "none", "sigma_K": sigma_k,
+                   "l2": "inputs larger than L2 (events 4 B x C = %.0f MB; G %.2f GB); no flush" %
+                         (4 * C / 1e6, 8 * P_pad * Ny * nkx / 1e9),
+                   "parallelism": f"replicas x{world} (independent datasets, no collective)"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(ach / hbm, 3), "traffic": traffic,
+                     "peak_source": hsrc, "algorithmic_bytes": sb[dom]},
+        "stages": stages,
+        "clocks": clk.summary(),
+    }
+
+    # ---- end to end through the public API with host buffers -------------
+    if not args.no_e2e:
+        h_idx = idx.cpu().pin_memory()
+        h_off = off.cpu().pin_memory()
+        h_phase = torch.empty_like(phase, device="cpu").pin_memory()
+        h_var = torch.empty(1, dtype=torch.float64).pin_memory()
+        d_idx = torch.empty_like(idx)
+        d_off = torch.empty_like(off)
+
+        def e2e_step():
+            d_idx.copy_(h_idx, non_blocking=True)
+            d_off.copy_(h_off, non_blocking=True)
+            step(d_idx, d_off)
+            h_phase.copy_(phase, non_blocking=True)
+            h_var.copy_(var, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        e_ms = torch.tensor([a.elapsed_time(b) / args.steps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
+        out["e2e"] = {"value": world * C / (float(e_ms.item()) * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": h_idx.numel() * 4 + h_off.numel() * 8,
+                      "d2h_bytes_per_step": h_phase.numel() * 4 + 8,
+                      "ms_per_step": float(e_ms.item())}
+
+    # ---- refocus: fused adjoint step replayed as a CUDA graph ----------------
+    if args.refocus_steps > 0:
+        th = torch.zeros(5, dtype=torch.float64, device=dev)
+        stepv = torch.tensor([1e3, 1e3, 1e3, 0.0, 0.0], dtype=torch.float64, device=dev)
+        rv = torch.empty(1, dtype=torch.float64, device=dev)
+        rg = torch.empty(5, dtype=torch.float64, device=dev)
+        rph = torch.empty(Ny, w.scan_nx, dtype=torch.float32, device=dev)
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                P.ssb_refocus_step(rec.plan, rec.G, th, stepv, rec.scratch, rv, rg, rph, rec.status)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            P.ssb_refocus_step(rec.plan, rec.G, th, stepv, rec.scratch, rv, rg, rph, rec.status)
+        lat = []
+        for _ in range(args.refocus_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+        lat.sort()
+        # plain form: one unbatched forward evaluation (trotter + inverse + variance)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var, status=rec.status)
+        b.record()
+        torch.cuda.synchronize()
+        out["refocus"] = {"ms_p50": lat[len(lat) // 2], "ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                          "replays": len(lat), "graph": True,
+                          "step": "V, dV/dtheta, phi and ascent update (one pass over G)",
+                          "forward_only_ms": a.elapsed_time(b) / 20}
+        rec.check()
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ---------
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_ev, ts, ws = time_oracle(256, str(dev), reps=1)
+        out["cpu_baseline"] = {"value": n_ev / ts[0], "unit": UNIT, "cores": cpu_threads(),
+                               "kind": "oracle",
+                               "sample": f"256x256 scan of the same detector geometry and dose "
+                                         f"({n_ev} events), whole oracle path, one run",
+                               "seconds": ts[0], "affinity_cores": len(os.sched_getaffinity(0))}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * eer4d.h -- C ABI of libeer4d.so: linear-index electron-event (EER) data to
+ * COM-DPC and single-sideband (SSB) phase-contrast images on one GB300 GPU.
+ *
+ * Paper: Pelz et al., "Real-time interactive 4D-STEM phase-contrast imaging
+ * from electron event representation data" (arXiv 2104.06336).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - d_* arguments are device pointers; h_* arguments are host pointers.  The
+ *   caller allocates and owns every buffer.  The library allocates device
+ *   memory only in eer4d_plan_create (small tables) and frees it in
+ *   eer4d_plan_destroy.  No entry point synchronises the device.
+ * - All work is enqueued on `stream` (a cudaStream_t; NULL is the legacy
+ *   default stream) and runs asynchronously.
+ * - Argument errors found on the host return a negative EER4D_E* code at once
+ *   and enqueue nothing.  Data errors found on the device (bad index, bad
+ *   offsets, count overflow, timeout) never trap: the offending events are
+ *   dropped, a bit is OR-ed into d_status[0] and counters are bumped.
+ *   d_status points to 4 uint32 words that the caller zeroes before use:
+ *     [0] EER4D_ST_* bits   [1] dropped events (idx >= W*H)
+ *     [2] pixel counts above 2048 in one frame   [3] reserved
+ *   eer4d_status_code() maps a copied-back status block to an EER4D_E* code.
+ * - A CUDA launch failure returns EER4D_ECUDA.
+ *
+ * Event data (Sec. II, Fig. 1b): frame f (scan position f = y*scan_nx + x,
+ * raster order) holds the events d_idx[d_off[f] .. d_off[f+1]) of the
+ * uint32 raw linear detector indices idx = y*det_w + x.  d_off is uint64
+ * with n_frames+1 entries indexing into d_idx, which has n_idx entries.
+ */
+#ifndef EER4D_H
+#define EER4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define EER4D_OK         0
+#define EER4D_EINVAL    -1  /* bad argument (host check) */
+#define EER4D_ERANGE    -2  /* event index >= det_w*det_h (device) */
+#define EER4D_EOFFSETS  -3  /* offsets decreasing or beyond n_idx (device) */
+#define EER4D_EOVERFLOW -4  /* a binned pixel got more than 2048 events in one frame (device) */
+#define EER4D_ETIMEOUT  -5  /* a bounded device wait gave up (device) */
+#define EER4D_ECUDA     -6  /* a CUDA call failed */
+#define EER4D_ENOMEM    -7  /* plan tables could not be allocated */
+#define EER4D_EORDER    -8  /* ssb_accumulate chunks not delivered in frame order */
+
+/* ---- device status bits (d_status[0]) ---------------------------------- */
+#define EER4D_ST_RANGE    0x01u
+#define EER4D_ST_OFFSETS  0x02u
+#define EER4D_ST_OVERFLOW 0x04u
+#define EER4D_ST_TIMEOUT  0x08u
+#define EER4D_ST_ROTATION 0x10u  /* candidates of one call differ in rotation */
+
+/* ---- plan options ------------------------------------------------------- */
+#define EER4D_FP32_FFT   0  /* scan transform: FP32 radix FFT */
+#define EER4D_SPLIT_FP16 1  /* scan transform: split hi+lo FP16 DFT on tensor cores */
+#define EER4D_NORM_NONE  0  /* Eq. 3 as printed: S(K) = sum over K(K) */
+#define EER4D_NORM_AREA  1  /* S(K) / |K(K)| (0 when the set is empty) */
+
+/* Detector, crop and scan geometry.  k = (u - dc_u, v - dc_v) is a binned
+ * detector pixel measured from the optical axis.  Binned pixel
+ * u = floor((x - crop_x0) / bin), v = floor((y - crop_y0) / bin),
+ * 0 <= u < pw, 0 <= v < ph.  Pixels with |k| < crop_px are kept (numbered
+ * row-major, v outer); those with |k|^2 < k0_px^2 (float32) are bright-field.
+ * Scan frequency index m (numpy fftfreq order) maps to K' = m * kpm binned
+ * pixels on each axis. */
+typedef struct eer4d_geom {
+  uint32_t det_w, det_h;      /* raw detector pixels */
+  uint32_t bin;               /* binning factor (>= 1) */
+  int32_t  crop_x0, crop_y0;  /* raw pixel where binned pixel 0 starts */
+  uint32_t pw, ph;            /* binned window */
+  uint32_t dc_u, dc_v;        /* binned pixel of the optical axis */
+  double   k0_px;             /* aperture radius alpha/dalpha (binned px) */
+  double   crop_px;           /* crop radius (binned px), >= k0_px */
+  uint32_t scan_ny, scan_nx;  /* scan positions (both even, 2..4096) */
+  double   kpm_y, kpm_x;      /* K' per scan frequency index (binned px) */
+  double   lambda_A;          /* electron wavelength (Angstrom) */
+  double   dalpha_rad;        /* binned pixel angle (rad) */
+  double   step_A;            /* scan step (Angstrom), for DPC frequencies */
+  double   dalpha_raw_rad;    /* raw pixel angle (rad), for COM units */
+} eer4d_geom;
+
+typedef struct eer4d_info {
+  int32_t P;        /* kept (cropped) pixels */
+  int32_t P_pad;    /* P rounded up to a multiple of 16: pixel stride of G */
+  int32_t P_bf;     /* bright-field pixels */
+  int32_t n_rows;   /* detector rows holding bright-field pixels */
+  int32_t nkx;      /* scan_nx/2 + 1 stored K_x columns of G */
+  int32_t trotter_list_max;  /* upper bound of |K(K)| + |K(-K)| */
+} eer4d_info;
+
+typedef struct eer4d_plan eer4d_plan;
+
+/* Aberrations are passed as double[5] per candidate, in this order:
+ *   C1 (defocus, A), C12a, C12b (two-fold astigmatism, A), C3 (spherical, A),
+ *   rot (scan rotation, rad; K' = R(rot) K'_0 counter-clockwise).
+ * chi(k) = 2 pi / lambda [C1 w^2/2 + (C12a (wx^2-wy^2) + C12b 2 wx wy)/2
+ *          + C3 w^4/4], w = k * dalpha_rad (Krivanek notation; the paper
+ * gives no formula), and the probe is A(k) = exp(-i chi(k)) inside |k| < k0. */
+
+/* ---- plan ---------------------------------------------------------------- */
+/* Validates the geometry, builds the pixel, row and FFT tables on the current
+ * device.  precision: EER4D_FP32_FFT or EER4D_SPLIT_FP16; norm:
+ * EER4D_NORM_NONE or EER4D_NORM_AREA.  Returns EINVAL for an invalid
+ * geometry (zero sizes, odd scan, crop_px < k0_px, more than 32767 kept
+ * pixels, scan side > 4096), ENOMEM/ECUDA when the tables cannot be made. */
+int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_plan** out);
+void eer4d_plan_destroy(eer4d_plan* plan);
+int eer4d_plan_info(const eer4d_plan* plan, eer4d_info* h_info);
+
+/* Bytes the caller allocates: counts (ssb_accumulate), G (the resident
+ * spectrum) and scratch (the largest need of com_dpc, ssb_reconstruct with
+ * n_cand candidates, ssb_grad and ssb_variance_grad). */
+int eer4d_workspace_bytes(const eer4d_plan* plan, int n_cand, size_t* counts_bytes,
+                          size_t* G_bytes, size_t* scratch_bytes);
+
+int eer4d_status_code(const uint32_t* h_status4);
+const char* eer4d_strerror(int code);
+/* Text of the last CUDA error seen by an entry point of the calling thread. */
+const char* eer4d_last_error(void);
+
+/* ---- a1: ingest and validate (Sec. II; Table 1 "sum all frames") ---------
+ * Checks the CSR (monotone offsets inside [0, n_idx], indices < W*H) and
+ * accumulates (adds to what the buffers hold) the PACBED histogram
+ * d_pacbed[H*W] (int64, nullable) and the integer totals d_totals[3] =
+ * (sum x, sum y, count) over all valid events (int64, nullable), whose ratio
+ * is the PACBED centre of mass used to centre the pattern (Sec. IV). */
+int eer_load_csr(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx,
+                 const uint64_t* d_off, uint64_t n_frames, int64_t* d_pacbed,
+                 int64_t* d_totals, uint32_t* d_status, void* stream);
+
+/* ---- a2 + a3: centre of mass and DPC (Eq. 4; Sec. V) -----------------------
+ * For the whole scan (n_frames = scan_ny*scan_nx): d_sums[3][F] (int64
+ * Sx, Sy, N per frame, exact), d_com[2][F] (float, COM - centre in raw px; 0
+ * for an empty frame) and, when d_phase is not NULL, the regularised Fourier
+ * integration phi = IFFT[-i (Kx Cx^ + Ky Cy^)/(lam1 + K^2 + lam2 K^4)]
+ * (DC = 0, C in 1/A = COM * dalpha_raw/lambda, K = fftfreq(N, step_A)).
+ * The centre is d_totals[0..1]/d_totals[2] when d_totals is not NULL, else
+ * (cx, cy).  d_scratch needs 8*F bytes when d_phase is not NULL. */
+int com_dpc(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+            int64_t* d_sums, float* d_com, float* d_phase, const int64_t* d_totals, double cx,
+            double cy, double lam1, double lam2, void* d_scratch, uint32_t* d_status, void* stream);
+
+/* ---- a4 + a5: bin/crop/densify and the G function (Table 1; Sec. IV) -------
+ * Scatters frames [first_frame, first_frame + n_frames) into d_counts
+ * (fp16 [P_pad][scan_ny*scan_nx], exact integers up to 2048), then runs the
+ * scan-axis DFT along x for every scan row completed by this chunk.  Chunks
+ * must arrive in frame order starting at frame 0 (else EORDER).  With
+ * is_last (the chunk ends at the last frame) the DFT along y completes
+ * G(k, K) = F_{R->K} counts in d_G: complex64 [scan_nx/2+1][scan_ny][P_pad]
+ * (K_x >= 0 half; G(k,-K) = conj G(k,K)), pixel innermost. */
+int ssb_accumulate(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                   uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
+                   int is_last, uint32_t* d_status, void* stream);
+
+/* ---- a6 + a7: SSB trotter integration and phase image (Eq. 3) --------------
+ * For each candidate c (d_aberr: double[n_cand][5] on the device, so a CUDA
+ * graph can replay with new values): S(K) = sum_{k in K(K)} G(k,K)
+ * exp(-i (chi(k) - chi(k - K'))) [/|K(K)|], and
+ * phi_c = (N_R/Gbar0) Im(IFFT2(S)), Gbar0 = mean of G(k,0) over bright-field
+ * pixels.  d_phase: float [n_cand][F] (nullable); d_var: double [n_cand]
+ * population variance of phi_c (nullable).  All candidates must share the
+ * rotation of candidate 0 (else EER4D_ST_ROTATION; the mask of candidate 0
+ * is used).  1 <= n_cand <= 1024. */
+int ssb_reconstruct(const eer4d_plan* plan, const void* d_G, const double* d_aberr, int n_cand,
+                    void* d_scratch, float* d_phase, double* d_var, uint32_t* d_status, void* stream);
+
+/* ---- a8: adjoint with respect to the aberrations ----------------------------
+ * d_grad[5] (double) = sum_R g(R) d phi(R)/d theta for theta = (C1, C12a,
+ * C12b, C3, rot) and the upstream gradient g = d_grad_phase (float [F]); the
+ * trotter mask is held fixed (it is piecewise constant in rot). */
+int ssb_grad(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
+             const float* d_grad_phase, double* d_grad, void* d_scratch, uint32_t* d_status,
+             void* stream);
+
+/* Fused refocus objective: V = variance of phi and dV/dtheta (double[5]) in
+ * one pass over G (Parseval: V = sum_K |Phi^(K)|^2 / N_R^2), plus phi
+ * (float [F], nullable). */
+int ssb_variance_grad(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
+                      void* d_scratch, float* d_phase, double* d_var, double* d_grad,
+                      uint32_t* d_status, void* stream);
+
+/* Diagnostic: d_count[F] (int32, [scan_ny][scan_nx] bins) = |K(K)| for the
+ * rotation d_aberr[4], from the same mask code the trotter kernel runs
+ * (set K of Sec. IV).  d_scratch as for ssb_reconstruct with one candidate. */
+int ssb_trotter_counts(const eer4d_plan* plan, const double* d_aberr, int32_t* d_count,
+                       void* d_scratch, void* stream);
+
+/* Refocus step (gradient ascent on the image variance, the interactive
+ * virtual-focus loop of Sec. IV / Fig. 2 driven by the adjoint): computes V,
+ * dV/dtheta and phi at d_aberr (as ssb_variance_grad), then updates in place
+ * d_aberr[j] += d_step[j] * dV/dtheta_j on the device.  Every operand lives
+ * on the device, so a CUDA graph of this call replays with the updated
+ * aberrations. */
+int ssb_refocus_step(const eer4d_plan* plan, const void* d_G, double* d_aberr, const double* d_step,
+                     void* d_scratch, float* d_phase, double* d_var, double* d_grad,
+                     uint32_t* d_status, void* stream);
+
+/* ---- measurement hooks (not part of the method) ------------------------------
+ * Stage ids for eer4d_set_stage_events. */
+#define EER4D_STAGE_VALIDATE 0  /* eer_load_csr */
+#define EER4D_STAGE_COM      1  /* per-frame COM sums (com_dpc) */
+#define EER4D_STAGE_DPC      2  /* Fourier integration (com_dpc) */
+#define EER4D_STAGE_SCATTER  3  /* bin/crop/densify (ssb_accumulate) */
+#define EER4D_STAGE_DFT_X    4  /* scan DFT along x (ssb_accumulate) */
+#define EER4D_STAGE_DFT_Y    5  /* scan DFT along y (ssb_accumulate, last chunk) */
+#define EER4D_STAGE_TROTTER  6  /* trotter integration / adjoint */
+#define EER4D_STAGE_IMAGE    7  /* variance and inverse transform to phi */
+#define EER4D_N_STAGES       8
+/* When set, each stage records ev_start[s] before and ev_stop[s] after its
+ * kernels on the launching stream.  The arrays hold EER4D_N_STAGES
+ * cudaEvent_t owned by the caller (NULL entries are skipped); passing NULL
+ * arrays clears the hook. */
+int eer4d_set_stage_events(eer4d_plan* plan, void* const* ev_start, void* const* ev_stop);
+/* Number of kernels the library has launched in this process. */
+uint64_t eer4d_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EER4D_H */

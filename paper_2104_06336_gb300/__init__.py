@@ -1,0 +1,24 @@
+"""GB300-native EER -> COM-DPC / SSB phase-contrast imaging (arXiv 2104.06336).
+
+The compute path is libeer4d.so (hand-written sm_103a CUDA kernels behind the
+C ABI of include/eer4d.h); this package is its Python binding.
+"""
+
+from . import _lib
+from ._lib import (  # noqa: F401  (C-ABI names)
+    Plan, Eer4dError, eer_load_csr, com_dpc, ssb_accumulate, ssb_reconstruct, ssb_grad,
+    ssb_variance_grad, ssb_trotter_counts, ssb_refocus_step, eer4d_set_stage_events,
+    eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, NORM_NONE, NORM_AREA,
+)
+from .pipeline import Reconstructor  # noqa: F401
+from .autograd import SSBPhase, ssb_phase  # noqa: F401
+
+
+def build(force: bool = False) -> str:
+    """Compiles libeer4d.so in-tree for sm_103a and returns its path."""
+    from .buildlib import build as _build
+    return _build(force=force)
+
+
+def load():
+    return _lib.load()

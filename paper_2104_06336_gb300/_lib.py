@@ -1,0 +1,231 @@
+"""ctypes binding of libeer4d.so (include/eer4d.h): argument marshalling only.
+
+Every function here forwards to the C ABI with device pointers taken from
+torch CUDA tensors and the current torch stream.  There is no CPU fallback:
+if the library is missing or a tensor is not on the GPU, the call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libeer4d.so")
+
+EER4D_OK, EER4D_EINVAL, EER4D_ERANGE, EER4D_EOFFSETS = 0, -1, -2, -3
+EER4D_EOVERFLOW, EER4D_ETIMEOUT, EER4D_ECUDA, EER4D_ENOMEM, EER4D_EORDER = -4, -5, -6, -7, -8
+ST_RANGE, ST_OFFSETS, ST_OVERFLOW, ST_TIMEOUT, ST_ROTATION = 0x1, 0x2, 0x4, 0x8, 0x10
+FP32_FFT, SPLIT_FP16 = 0, 1
+NORM_NONE, NORM_AREA = 0, 1
+
+EXPORTS = [
+    "eer4d_plan_create", "eer4d_plan_destroy", "eer4d_plan_info", "eer4d_workspace_bytes",
+    "eer4d_status_code", "eer4d_strerror", "eer4d_last_error", "eer_load_csr", "com_dpc",
+    "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
+    "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count",
+]
+STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image"]
+
+
+class Geom(C.Structure):
+    _fields_ = [
+        ("det_w", C.c_uint32), ("det_h", C.c_uint32), ("bin", C.c_uint32),
+        ("crop_x0", C.c_int32), ("crop_y0", C.c_int32),
+        ("pw", C.c_uint32), ("ph", C.c_uint32), ("dc_u", C.c_uint32), ("dc_v", C.c_uint32),
+        ("k0_px", C.c_double), ("crop_px", C.c_double),
+        ("scan_ny", C.c_uint32), ("scan_nx", C.c_uint32),
+        ("kpm_y", C.c_double), ("kpm_x", C.c_double),
+        ("lambda_A", C.c_double), ("dalpha_rad", C.c_double), ("step_A", C.c_double),
+        ("dalpha_raw_rad", C.c_double),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [("P", C.c_int32), ("P_pad", C.c_int32), ("P_bf", C.c_int32), ("n_rows", C.c_int32),
+                ("nkx", C.c_int32), ("trotter_list_max", C.c_int32)]
+
+
+_lib = None
+
+
+class Eer4dError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.eer4d_strerror(code).decode()
+        if code == EER4D_ECUDA:
+            msg += ": " + lib.eer4d_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Loads libeer4d.so (building it first is the caller's job: build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libeer4d.so not found at {path}; run paper_2104_06336_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, U32, U64, I32, D, S = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_double, C.c_size_t
+    sig = {
+        "eer4d_plan_create": (I32, [C.POINTER(Geom), I32, I32, C.POINTER(C.c_void_p)]),
+        "eer4d_plan_destroy": (None, [P]),
+        "eer4d_plan_info": (I32, [P, C.POINTER(Info)]),
+        "eer4d_workspace_bytes": (I32, [P, I32, C.POINTER(S), C.POINTER(S), C.POINTER(S)]),
+        "eer4d_status_code": (I32, [C.POINTER(U32)]),
+        "eer4d_strerror": (C.c_char_p, [I32]),
+        "eer4d_last_error": (C.c_char_p, []),
+        "eer_load_csr": (I32, [P, P, U64, P, U64, P, P, P, P]),
+        "com_dpc": (I32, [P, P, U64, P, P, P, P, P, D, D, D, D, P, P, P]),
+        "ssb_accumulate": (I32, [P, P, U64, P, U64, U64, P, P, I32, P, P]),
+        "ssb_reconstruct": (I32, [P, P, P, I32, P, P, P, P, P]),
+        "ssb_grad": (I32, [P, P, P, P, P, P, P, P]),
+        "ssb_variance_grad": (I32, [P, P, P, P, P, P, P, P, P]),
+        "ssb_trotter_counts": (I32, [P, P, P, P, P]),
+        "ssb_refocus_step": (I32, [P, P, P, P, P, P, P, P, P, P]),
+        "eer4d_set_stage_events": (I32, [P, P, P]),
+        "eer4d_launch_count": (C.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != EER4D_OK:
+        raise Eer4dError(rc, where)
+
+
+def status_code(status: torch.Tensor) -> int:
+    h = status.detach().to("cpu", torch.int64).numpy().astype("uint32")
+    arr = (C.c_uint32 * 4)(*[int(v) for v in h[:4]])
+    return load().eer4d_status_code(arr)
+
+
+class Plan:
+    """An eer4d_plan on the current CUDA device (geometry dict with the field
+    names of eer4d_geom)."""
+
+    def __init__(self, geom: dict, precision: int = FP32_FFT, norm: int = NORM_NONE):
+        lib = load()
+        g = Geom(**{k: geom[k] for k, _ in Geom._fields_})
+        h = C.c_void_p()
+        _check(lib.eer4d_plan_create(C.byref(g), precision, norm, C.byref(h)), "eer4d_plan_create")
+        self._h = h
+        self.geom = dict(geom)
+        self.precision = precision
+        self.norm = norm
+        info = Info()
+        _check(lib.eer4d_plan_info(h, C.byref(info)), "eer4d_plan_info")
+        self.info = {k: getattr(info, k) for k, _ in Info._fields_}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self, n_cand: int = 1):
+        c, g, s = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        _check(load().eer4d_workspace_bytes(self._h, n_cand, C.byref(c), C.byref(g), C.byref(s)),
+               "eer4d_workspace_bytes")
+        return c.value, g.value, s.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().eer4d_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- entry points, same names as the C ABI ---------------------------------
+def eer_load_csr(plan: Plan, idx, off, pacbed=None, totals=None, status=None):
+    _check(load().eer_load_csr(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                               off.numel() - 1, _ptr(pacbed, "pacbed"), _ptr(totals, "totals"),
+                               _ptr(status, "status"), _stream()), "eer_load_csr")
+
+
+def com_dpc(plan: Plan, idx, off, sums, com, phase=None, totals=None, cx=0.0, cy=0.0, lam1=0.0,
+            lam2=0.0, scratch=None, status=None):
+    _check(load().com_dpc(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                          _ptr(sums, "sums"), _ptr(com, "com"), _ptr(phase, "phase"),
+                          _ptr(totals, "totals"), float(cx), float(cy), float(lam1), float(lam2),
+                          _ptr(scratch, "scratch"), _ptr(status, "status"), _stream()), "com_dpc")
+
+
+def ssb_accumulate(plan: Plan, idx, off, first_frame: int, counts, G, is_last: bool, status=None):
+    _check(load().ssb_accumulate(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                                 int(first_frame), off.numel() - 1, _ptr(counts, "counts"),
+                                 _ptr(G, "G"), int(bool(is_last)), _ptr(status, "status"),
+                                 _stream()), "ssb_accumulate")
+
+
+def ssb_reconstruct(plan: Plan, G, aberr, scratch, phase=None, var=None, status=None):
+    n = aberr.numel() // 5
+    _check(load().ssb_reconstruct(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"), n,
+                                  _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
+                                  _ptr(status, "status"), _stream()), "ssb_reconstruct")
+
+
+def ssb_grad(plan: Plan, G, aberr, grad_phase, grad, scratch, status=None):
+    _check(load().ssb_grad(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
+                           _ptr(grad_phase, "grad_phase"), _ptr(grad, "grad"),
+                           _ptr(scratch, "scratch"), _ptr(status, "status"), _stream()), "ssb_grad")
+
+
+def ssb_variance_grad(plan: Plan, G, aberr, scratch, var, grad, phase=None, status=None):
+    _check(load().ssb_variance_grad(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
+                                    _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
+                                    _ptr(grad, "grad"), _ptr(status, "status"), _stream()),
+           "ssb_variance_grad")
+
+
+def ssb_trotter_counts(plan: Plan, aberr, count, scratch):
+    _check(load().ssb_trotter_counts(plan.handle, _ptr(aberr, "aberr"), _ptr(count, "count"),
+                                     _ptr(scratch, "scratch"), _stream()), "ssb_trotter_counts")
+
+
+def ssb_refocus_step(plan: Plan, G, aberr, step, scratch, var, grad, phase=None, status=None):
+    _check(load().ssb_refocus_step(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"), _ptr(step, "step"),
+                                   _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
+                                   _ptr(grad, "grad"), _ptr(status, "status"), _stream()),
+           "ssb_refocus_step")
+
+
+def eer4d_set_stage_events(plan: Plan, starts=None, stops=None):
+    """starts/stops: lists of len(STAGES) torch.cuda.Event (or None) or None to clear."""
+    if starts is None:
+        _check(load().eer4d_set_stage_events(plan.handle, None, None), "eer4d_set_stage_events")
+        return
+    arr_t = C.c_void_p * len(STAGES)
+    a = arr_t(*[C.c_void_p(e.cuda_event if e is not None else 0) for e in starts])
+    b = arr_t(*[C.c_void_p(e.cuda_event if e is not None else 0) for e in stops])
+    _check(load().eer4d_set_stage_events(plan.handle, a, b), "eer4d_set_stage_events")
+
+
+def eer4d_launch_count() -> int:
+    return int(load().eer4d_launch_count())

@@ -1,0 +1,367 @@
+// C ABI of libeer4d: plan construction and the entry points declared in
+// include/eer4d.h.  Host code only validates arguments, derives launch
+// parameters and enqueues kernels; every step of the path runs on the GPU.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+#include <atomic>
+#include <mutex>
+#include <map>
+#include <utility>
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+std::atomic<unsigned long long> g_launches{0};
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return EER4D_OK;
+  snprintf(g_last_error, sizeof g_last_error, "%s", cudaGetErrorString(e));
+  return EER4D_ECUDA;
+}
+
+int factorize(int N, int* radix) {
+  int n = N, k = 0;
+  while (n % 8 == 0) { radix[k++] = 8; n /= 8; }
+  while (n % 4 == 0) { radix[k++] = 4; n /= 4; }
+  while (n % 2 == 0) { radix[k++] = 2; n /= 2; }
+  for (int p = 3; n > 1; p += 2) {
+    while (n % p == 0) {
+      if (k >= EER4D_MAX_STAGES) return -1;
+      radix[k++] = p;
+      n /= p;
+    }
+  }
+  return k;
+}
+
+// twiddles exp(-2 pi i j / N) from the exact integer j, in double
+cudaError_t make_fft(int N, FftDesc& d, float2** dev) {
+  d.N = N;
+  d.nst = factorize(N, d.radix);
+  if (d.nst < 0) return cudaErrorInvalidValue;
+  std::vector<float2> tw(N);
+  const double tp = 6.283185307179586476925286766559;
+  for (int j = 0; j < N; ++j) {
+    tw[j] = make_float2((float)cos(tp * j / N), (float)-sin(tp * j / N));
+  }
+  cudaError_t e = cudaMalloc(dev, sizeof(float2) * N);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(*dev, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+  d.tw = *dev;
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(T** dev, const std::vector<T>& h) {
+  cudaError_t e = cudaMalloc(dev, sizeof(T) * (h.empty() ? 1 : h.size()));
+  if (e != cudaSuccess) return e;
+  if (h.empty()) return cudaSuccess;
+  return cudaMemcpy(*dev, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+bool geom_ok(const eer4d_geom* g) {
+  if (!g) return false;
+  if (g->det_w == 0 || g->det_h == 0 || (uint64_t)g->det_w * g->det_h > 0xFFFFFFFFull) return false;
+  if (g->det_w > 32767 || g->det_h > 32767) return false;
+  if (g->bin == 0 || g->pw == 0 || g->ph == 0 || g->dc_u >= g->pw || g->dc_v >= g->ph) return false;
+  if (g->pw > 32767 || g->ph > 32767) return false;
+  if (!(g->k0_px > 0.0) || !(g->crop_px >= g->k0_px)) return false;
+  if (g->scan_ny < 2 || g->scan_nx < 2 || g->scan_ny > 4096 || g->scan_nx > 4096) return false;
+  if ((g->scan_ny & 1) || (g->scan_nx & 1)) return false;
+  if (!(g->kpm_x > 0.0) || !(g->kpm_y > 0.0) || !(g->lambda_A > 0.0) || !(g->dalpha_rad > 0.0)) return false;
+  if (!(g->step_A > 0.0) || !(g->dalpha_raw_rad > 0.0)) return false;
+  return true;
+}
+
+void free_plan(eer4d_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_lutx);
+  cudaFree(p->d_luty);
+  cudaFree(p->d_lut2);
+  cudaFree(p->d_pix);
+  cudaFree(p->d_rows);
+  cudaFree(p->d_tw_y);
+  cudaFree(p->d_tw_x);
+  free(p);
+}
+
+}  // namespace
+
+void stage_begin(const eer4d_plan* p, int stage, cudaStream_t s) {
+  if (p && p->ev_start[stage]) cudaEventRecord(p->ev_start[stage], s);
+}
+void stage_end(const eer4d_plan* p, int stage, cudaStream_t s) {
+  if (p && p->ev_stop[stage]) cudaEventRecord(p->ev_stop[stage], s);
+}
+cudaError_t ensure_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;  // (kernel, device) -> bytes set
+  std::lock_guard<std::mutex> lk(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<const void*, int> key(kernel, dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
+}
+
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+extern "C" {
+
+uint64_t eer4d_launch_count(void) { return g_launches.load(); }
+
+int eer4d_set_stage_events(eer4d_plan* p, void* const* ev_start, void* const* ev_stop) {
+  if (!p) return EER4D_EINVAL;
+  for (int i = 0; i < EER4D_N_STAGES; ++i) {
+    p->ev_start[i] = ev_start ? static_cast<cudaEvent_t>(ev_start[i]) : nullptr;
+    p->ev_stop[i] = ev_stop ? static_cast<cudaEvent_t>(ev_stop[i]) : nullptr;
+  }
+  return EER4D_OK;
+}
+
+const char* eer4d_last_error(void) { return g_last_error; }
+
+int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_plan** out) {
+  if (!out) return EER4D_EINVAL;
+  *out = nullptr;
+  if (!geom_ok(h_geom)) return EER4D_EINVAL;
+  if (precision != EER4D_FP32_FFT && precision != EER4D_SPLIT_FP16) return EER4D_EINVAL;
+  if (norm != EER4D_NORM_NONE && norm != EER4D_NORM_AREA) return EER4D_EINVAL;
+  const eer4d_geom& g = *h_geom;
+  eer4d_plan* p = static_cast<eer4d_plan*>(calloc(1, sizeof(eer4d_plan)));
+  if (!p) return EER4D_ENOMEM;
+  p->g = g;
+  p->precision = precision;
+  p->norm = norm;
+  p->F = (int)(g.scan_ny * g.scan_nx);
+  p->nkx = (int)g.scan_nx / 2 + 1;
+  p->dw.init(g.det_w);
+
+  // kept pixels (|k| < crop, double) numbered row-major; bright-field
+  // |k|^2 < k0^2 in float32
+  std::vector<int32_t> lut2((size_t)g.pw * g.ph, -1);
+  std::vector<short2> pix;
+  std::vector<int4> rows;
+  const double crop2 = g.crop_px * g.crop_px;
+  const float k0sq = (float)(g.k0_px * g.k0_px);
+  int P_bf = 0;
+  for (uint32_t v = 0; v < g.ph; ++v) {
+    const int ky = (int)v - (int)g.dc_v;
+    int lo = 1, hi = 0, plo = -1;
+    for (uint32_t u = 0; u < g.pw; ++u) {
+      const int kx = (int)u - (int)g.dc_u;
+      if ((double)(kx * kx + ky * ky) < crop2) {
+        const int idx = (int)pix.size();
+        lut2[(size_t)v * g.pw + u] = idx;
+        pix.push_back(make_short2((short)kx, (short)ky));
+        if ((float)(kx * kx + ky * ky) < k0sq) {
+          if (lo > hi) { lo = kx; plo = idx; }
+          if (kx != hi + 1 && hi >= lo) { free_plan(p); return EER4D_EINVAL; }
+          hi = kx;
+          ++P_bf;
+        }
+      }
+    }
+    if (lo <= hi) rows.push_back(make_int4(ky, lo, hi, plo));
+  }
+  p->P = (int)pix.size();
+  if (p->P == 0 || p->P > 32767 || P_bf == 0) { free_plan(p); return EER4D_EINVAL; }
+  p->P_bf = P_bf;
+  p->P_pad = (p->P + 15) / 16 * 16;
+  p->n_rows = (int)rows.size();
+  p->list_max = (P_bf + 1) & ~1;
+  pix.resize(p->P_pad, make_short2(0, 0));
+
+  std::vector<int16_t> lutx(g.det_w), luty(g.det_h);
+  for (uint32_t x = 0; x < g.det_w; ++x) {
+    const long long d = (long long)x - g.crop_x0;
+    const long long u = d >= 0 ? d / g.bin : -1;
+    lutx[x] = (int16_t)((d >= 0 && u < (long long)g.pw) ? u : -1);
+  }
+  for (uint32_t y = 0; y < g.det_h; ++y) {
+    const long long d = (long long)y - g.crop_y0;
+    const long long v = d >= 0 ? d / g.bin : -1;
+    luty[y] = (int16_t)((d >= 0 && v < (long long)g.ph) ? v : -1);
+  }
+  cudaError_t e;
+  if ((e = upload(&p->d_lutx, lutx)) != cudaSuccess || (e = upload(&p->d_luty, luty)) != cudaSuccess ||
+      (e = upload(&p->d_lut2, lut2)) != cudaSuccess || (e = upload(&p->d_pix, pix)) != cudaSuccess ||
+      (e = upload(&p->d_rows, rows)) != cudaSuccess ||
+      (e = make_fft((int)g.scan_ny, p->fy, &p->d_tw_y)) != cudaSuccess ||
+      (e = make_fft((int)g.scan_nx, p->fx, &p->d_tw_x)) != cudaSuccess) {
+    const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
+    free_plan(p);
+    return rc;
+  }
+  p->next_frame = 0;
+  *out = p;
+  return EER4D_OK;
+}
+
+void eer4d_plan_destroy(eer4d_plan* plan) { free_plan(plan); }
+
+int eer4d_plan_info(const eer4d_plan* p, eer4d_info* info) {
+  if (!p || !info) return EER4D_EINVAL;
+  info->P = p->P;
+  info->P_pad = p->P_pad;
+  info->P_bf = p->P_bf;
+  info->n_rows = p->n_rows;
+  info->nkx = p->nkx;
+  info->trotter_list_max = 2 * p->P_bf;
+  return EER4D_OK;
+}
+
+int eer4d_workspace_bytes(const eer4d_plan* p, int n_cand, size_t* counts_bytes, size_t* G_bytes,
+                          size_t* scratch_bytes) {
+  if (!p || n_cand < 1 || n_cand > 1024) return EER4D_EINVAL;
+  if (counts_bytes) *counts_bytes = (size_t)2 * p->P_pad * p->F;
+  if (G_bytes) *G_bytes = sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
+  if (scratch_bytes) {
+    size_t s = sizeof(float2) * (size_t)p->F;  // com_dpc
+    size_t r = trotter_scratch_bytes(p, n_cand, TROT_FWD);
+    if (r > s) s = r;
+    r = trotter_scratch_bytes(p, 1, TROT_GRAD) + sizeof(float2) * (size_t)p->g.scan_ny * p->nkx;
+    if (r > s) s = r;
+    r = trotter_scratch_bytes(p, 1, TROT_VARGRAD);
+    if (r > s) s = r;
+    *scratch_bytes = s;
+  }
+  return EER4D_OK;
+}
+
+int eer4d_status_code(const uint32_t* st) {
+  if (!st) return EER4D_EINVAL;
+  const uint32_t b = st[0];
+  if (b & EER4D_ST_OFFSETS) return EER4D_EOFFSETS;
+  if (b & EER4D_ST_RANGE) return EER4D_ERANGE;
+  if (b & EER4D_ST_OVERFLOW) return EER4D_EOVERFLOW;
+  if (b & EER4D_ST_TIMEOUT) return EER4D_ETIMEOUT;
+  if (b & EER4D_ST_ROTATION) return EER4D_EINVAL;
+  return EER4D_OK;
+}
+
+const char* eer4d_strerror(int code) {
+  switch (code) {
+    case EER4D_OK: return "ok";
+    case EER4D_EINVAL: return "invalid argument";
+    case EER4D_ERANGE: return "event index outside the detector (events dropped)";
+    case EER4D_EOFFSETS: return "frame offsets decreasing or beyond the event array";
+    case EER4D_EOVERFLOW: return "more than 2048 events in one binned pixel of one frame";
+    case EER4D_ETIMEOUT: return "a bounded device wait timed out";
+    case EER4D_ECUDA: return "CUDA error";
+    case EER4D_ENOMEM: return "out of memory";
+    case EER4D_EORDER: return "chunks not delivered in frame order";
+    default: return "unknown error";
+  }
+}
+
+int eer_load_csr(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                 uint64_t n_frames, int64_t* d_pacbed, int64_t* d_totals, uint32_t* d_status,
+                 void* stream) {
+  if (!p || !d_off || (n_idx && !d_idx)) return EER4D_EINVAL;
+  if (n_frames == 0) return EER4D_OK;
+  return cuda_fail(launch_validate(p, d_idx, n_idx, d_off, n_frames, d_pacbed, d_totals, d_status,
+                                   (cudaStream_t)stream));
+}
+
+int com_dpc(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+            int64_t* d_sums, float* d_com, float* d_phase, const int64_t* d_totals, double cx,
+            double cy, double lam1, double lam2, void* d_scratch, uint32_t* d_status, void* stream) {
+  if (!p || !d_off || (n_idx && !d_idx) || !d_sums || !d_com) return EER4D_EINVAL;
+  if (d_phase && !d_scratch) return EER4D_EINVAL;
+  if (!(lam1 >= 0.0) || !(lam2 >= 0.0)) return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* z = d_phase ? static_cast<float2*>(d_scratch) : nullptr;
+  int rc = cuda_fail(launch_com(p, d_idx, n_idx, d_off, d_sums, d_com, z, d_totals, cx, cy,
+                                d_status, s));
+  if (rc != EER4D_OK || !d_phase) return rc;
+  return cuda_fail(launch_idpc(p, z, d_phase, lam1, lam2, s));
+}
+
+int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                   uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G, int is_last,
+                   uint32_t* d_status, void* stream) {
+  if (!p || !d_off || (n_idx && !d_idx) || !d_counts || !d_G) return EER4D_EINVAL;
+  const uint64_t F = (uint64_t)p->F;
+  const uint64_t end = first_frame + n_frames;
+  if (end > F || end < first_frame) return EER4D_EINVAL;
+  if (is_last && end != F) return EER4D_EINVAL;
+  if (first_frame == 0) p->next_frame = 0;
+  if (first_frame != p->next_frame) return EER4D_EORDER;
+  cudaStream_t s = (cudaStream_t)stream;
+  __half* counts = static_cast<__half*>(d_counts);
+  float2* G = static_cast<float2*>(d_G);
+  int rc = cuda_fail(launch_scatter(p, d_idx, n_idx, d_off, first_frame, n_frames, counts,
+                                    d_status, s));
+  if (rc != EER4D_OK) return rc;
+  const uint64_t Nx = p->g.scan_nx;
+  rc = cuda_fail(launch_stage1(p, counts, G, (int)(first_frame / Nx), (int)(end / Nx), s));
+  if (rc != EER4D_OK) return rc;
+  p->next_frame = end;
+  if (is_last) {
+    rc = cuda_fail(launch_stage2(p, G, s));
+    p->next_frame = 0;
+  }
+  return rc;
+}
+
+int ssb_reconstruct(const eer4d_plan* p, const void* d_G, const double* d_aberr, int n_cand,
+                    void* d_scratch, float* d_phase, double* d_var, uint32_t* d_status,
+                    void* stream) {
+  if (!p || !d_G || !d_aberr || !d_scratch || n_cand < 1 || n_cand > 1024) return EER4D_EINVAL;
+  return cuda_fail(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, n_cand, TROT_FWD,
+                                  d_scratch, nullptr, d_phase, d_var, nullptr, nullptr, d_status,
+                                  (cudaStream_t)stream));
+}
+
+int ssb_grad(const eer4d_plan* p, const void* d_G, const double* d_aberr, const float* d_grad_phase,
+             double* d_grad, void* d_scratch, uint32_t* d_status, void* stream) {
+  if (!p || !d_G || !d_aberr || !d_grad_phase || !d_grad || !d_scratch) return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* W = reinterpret_cast<float2*>(static_cast<unsigned char*>(d_scratch) +
+                                        trotter_scratch_bytes(p, 1, TROT_GRAD));
+  int rc = cuda_fail(launch_r2c_image(p, d_grad_phase, W, s));
+  if (rc != EER4D_OK) return rc;
+  return cuda_fail(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_GRAD,
+                                  d_scratch, W, nullptr, nullptr, d_grad, nullptr, d_status, s));
+}
+
+int ssb_variance_grad(const eer4d_plan* p, const void* d_G, const double* d_aberr, void* d_scratch,
+                      float* d_phase, double* d_var, double* d_grad, uint32_t* d_status,
+                      void* stream) {
+  if (!p || !d_G || !d_aberr || !d_scratch || !d_var || !d_grad) return EER4D_EINVAL;
+  return cuda_fail(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_VARGRAD,
+                                  d_scratch, nullptr, d_phase, d_var, d_grad, nullptr, d_status,
+                                  (cudaStream_t)stream));
+}
+
+int ssb_refocus_step(const eer4d_plan* p, const void* d_G, double* d_aberr, const double* d_step,
+                     void* d_scratch, float* d_phase, double* d_var, double* d_grad,
+                     uint32_t* d_status, void* stream) {
+  if (!p || !d_G || !d_aberr || !d_step || !d_scratch || !d_var || !d_grad) return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_fail(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_VARGRAD,
+                                    d_scratch, nullptr, d_phase, d_var, d_grad, nullptr, d_status, s));
+  if (rc != EER4D_OK) return rc;
+  return cuda_fail(launch_ascent(d_aberr, d_step, d_grad, s));
+}
+
+int ssb_trotter_counts(const eer4d_plan* p, const double* d_aberr, int32_t* d_count,
+                       void* d_scratch, void* stream) {
+  if (!p || !d_aberr || !d_count || !d_scratch) return EER4D_EINVAL;
+  return cuda_fail(launch_trotter(p, nullptr, d_aberr, 1, TROT_COUNT, d_scratch, nullptr, nullptr,
+                                  nullptr, nullptr, d_count, nullptr, (cudaStream_t)stream));
+}
+
+}  // extern "C"

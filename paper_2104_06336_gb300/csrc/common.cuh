@@ -1,0 +1,145 @@
+// Shared device helpers and the internal plan of libeer4d (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "eer4d.h"
+
+#define EER4D_MAX_STAGES 16
+#define EER4D_WARPS_TROTTER 8
+
+// ---------------------------------------------------------------- complex ---
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (dir = +1) or +i (dir = -1)
+__device__ __forceinline__ float2 cmul_mi(float2 a, int dir) {
+  return dir > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// ------------------------------------------------------- integer division ---
+// Exact floor division of a uint32 by a runtime divisor d >= 1:
+// q0 = umulhi(n, floor(2^32/d)) is q or q-1, one correction makes it exact.
+struct DivMod {
+  uint32_t d, m;
+  __host__ void init(uint32_t div) {
+    d = div;
+    m = div == 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / div);
+  }
+  __device__ __forceinline__ void divmod(uint32_t n, uint32_t& q, uint32_t& r) const {
+    q = __umulhi(n, m);
+    r = n - q * d;
+    if (r >= d) { q += 1; r -= d; }
+  }
+};
+
+// ---------------------------------------------------------------- FFT plan ---
+// Stockham radix-decomposition of one transform length; twiddles tw[j] =
+// exp(-2 pi i j / N) made on the host in double from the exact integer j.
+struct FftDesc {
+  int N;
+  int nst;
+  int radix[EER4D_MAX_STAGES];
+  const float2* tw;
+};
+
+// ------------------------------------------------------------- plan state ---
+struct eer4d_plan {
+  eer4d_geom g;
+  int precision, norm;
+  int P, P_pad, P_bf, n_rows, nkx, list_max;
+  int F;
+  DivMod dw;                 // division by det_w
+  // device tables (owned)
+  int16_t* d_lutx;           // [det_w] binned u or -1
+  int16_t* d_luty;           // [det_h] binned v or -1
+  int32_t* d_lut2;           // [ph*pw] kept pixel index or -1
+  short2* d_pix;             // [P_pad] (kx, ky)
+  int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
+  float2* d_tw_y;            // [scan_ny]
+  float2* d_tw_x;            // [scan_nx]
+  FftDesc fy, fx;
+  // streaming state of ssb_accumulate (host)
+  uint64_t next_frame;
+  // optional per-stage timing events (caller-owned cudaEvent_t), see
+  // eer4d_set_stage_events
+  cudaEvent_t ev_start[EER4D_N_STAGES];
+  cudaEvent_t ev_stop[EER4D_N_STAGES];
+};
+
+// stage timing: records the caller's events around a launch group on the
+// launching stream; counts kernel launches for eer4d_launch_count
+void stage_begin(const eer4d_plan* p, int stage, cudaStream_t s);
+void stage_end(const eer4d_plan* p, int stage, cudaStream_t s);
+void count_launches(int n);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`; remembers
+// what it set so repeated launches (and graph captures) make no further call.
+cudaError_t ensure_smem(const void* kernel, size_t bytes);
+
+// ---------------------------------------------------------- status helpers ---
+__device__ __forceinline__ void st_or(uint32_t* st, uint32_t bits) {
+  if (st) atomicOr(st, bits);
+}
+__device__ __forceinline__ void st_add(uint32_t* st, int word, uint32_t n) {
+  if (st && n) atomicAdd(st + word, n);
+}
+
+// ------------------------------------------------------------ warp helpers ---
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
+  int lane = threadIdx.x & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// signed frequency index of bin m of an N-point DFT (numpy fftfreq order)
+__host__ __device__ __forceinline__ int freq_index(int m, int N) { return (2 * m < N) ? m : m - N; }
+
+// ------------------------------------------------------ internal launchers ---
+// (defined in the .cu files; all return cudaError_t of the launch)
+cudaError_t launch_validate(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
+                            const uint64_t* off, uint64_t n_frames, int64_t* pacbed,
+                            int64_t* totals, uint32_t* st, cudaStream_t s);
+cudaError_t launch_com(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx, const uint64_t* off,
+                       int64_t* sums, float* com, float2* z, const int64_t* totals, double cx,
+                       double cy, uint32_t* st, cudaStream_t s);
+cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
+                           const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
+                           uint32_t* st, cudaStream_t s);
+cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
+                          cudaStream_t s);
+cudaError_t launch_stage2(const eer4d_plan* p, float2* G, cudaStream_t s);
+cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam1, double lam2,
+                        cudaStream_t s);
+cudaError_t launch_c2r_image(const eer4d_plan* p, float2* H, float* phase, int n_cand, cudaStream_t s);
+cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cudaStream_t s);
+
+// trotter modes
+enum { TROT_FWD = 0, TROT_GRAD = 1, TROT_VARGRAD = 2, TROT_COUNT = 3 };
+cudaError_t launch_ascent(double* theta, const double* step, const double* grad, cudaStream_t s);
+size_t trotter_scratch_bytes(const eer4d_plan* p, int n_cand, int mode);
+cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* aberr, int n_cand,
+                           int mode, void* scratch, const float2* W, float* phase_out,
+                           double* var_out, double* grad_out, int32_t* count_out, uint32_t* st,
+                           cudaStream_t s);

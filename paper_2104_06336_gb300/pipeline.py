@@ -1,0 +1,121 @@
+"""Device buffers around one plan: the user-facing path EER -> COM/DPC and SSB.
+
+PyTorch only allocates device memory and supplies the stream; every step runs
+in libeer4d's kernels through the C ABI (``_lib``).
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+
+def as_u32(idx: torch.Tensor) -> torch.Tensor:
+    """int32 or uint32 storage of raw linear indices, as the C ABI reads them."""
+    if idx.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError("event indices must be 32-bit integers (uint32 values)")
+    return idx.contiguous()
+
+
+class Reconstructor:
+    """Plan + workspace for one scan geometry on one GPU.
+
+    ``geom`` uses the field names of eer4d_geom.  Buffers:
+    counts fp16 [P_pad][F], G complex64 [nkx][Ny][P_pad], scratch bytes,
+    status int32[4] (zeroed at construction; see ``check``)."""
+
+    def __init__(self, geom: dict, precision: int = L.FP32_FFT, norm: int = L.NORM_NONE,
+                 n_cand: int = 1, device=None, alloc_counts: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Reconstructor needs a CUDA GPU; there is no CPU path")
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.plan = L.Plan(geom, precision, norm)
+            cb, gb, sb = self.plan.workspace_bytes(n_cand)
+            self.n_cand = n_cand
+            self.counts = torch.empty(cb // 2, dtype=torch.float16, device=self.device) if alloc_counts else None
+            self.G = torch.empty(gb // 4, dtype=torch.float32, device=self.device)
+            self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+            self.status = torch.zeros(4, dtype=torch.int32, device=self.device)
+            self.totals = torch.zeros(3, dtype=torch.int64, device=self.device)
+        self.geom = dict(geom)
+        self.Ny, self.Nx = geom["scan_ny"], geom["scan_nx"]
+        self.F = self.Ny * self.Nx
+        self.info = self.plan.info
+
+    # -- ingest ---------------------------------------------------------------
+    def load(self, idx: torch.Tensor, off: torch.Tensor, chunk_frames: int | None = None,
+             pacbed: torch.Tensor | None = None):
+        """Validates the CSR (totals for the PACBED centre) and builds G
+        (ssb_accumulate over chunks of ``chunk_frames`` frames)."""
+        idx = as_u32(idx)
+        off = off.contiguous()
+        self.totals.zero_()
+        L.eer_load_csr(self.plan, idx, off, pacbed=pacbed, totals=self.totals, status=self.status)
+        self.accumulate(idx, off, chunk_frames)
+
+    def accumulate(self, idx: torch.Tensor, off: torch.Tensor, chunk_frames: int | None = None):
+        F = self.F
+        step = F if chunk_frames is None else int(chunk_frames)
+        for f0 in range(0, F, step):
+            f1 = min(F, f0 + step)
+            L.ssb_accumulate(self.plan, idx, off[f0:f1 + 1], f0, self.counts, self.G, f1 == F,
+                             status=self.status)
+
+    def com_dpc(self, idx: torch.Tensor, off: torch.Tensor, lam1=0.0, lam2=0.0, use_totals=True,
+                cx=0.0, cy=0.0, phase=True):
+        """Per-frame COM sums, COM maps and the Fourier-integrated DPC phase."""
+        sums = torch.empty(3, self.F, dtype=torch.int64, device=self.device)
+        com = torch.empty(2, self.F, dtype=torch.float32, device=self.device)
+        ph = torch.empty(self.Ny, self.Nx, dtype=torch.float32, device=self.device) if phase else None
+        L.com_dpc(self.plan, as_u32(idx), off.contiguous(), sums, com, ph,
+                  totals=self.totals if use_totals else None, cx=cx, cy=cy, lam1=lam1, lam2=lam2,
+                  scratch=self.scratch, status=self.status)
+        return sums, com, ph
+
+    # -- SSB -----------------------------------------------------------------
+    def reconstruct(self, aberr: torch.Tensor, phase: bool = True):
+        """SSB phase images and variances for aberration candidates [n][5]."""
+        ab = aberr.to(self.device, torch.float64).reshape(-1, 5).contiguous()
+        n = ab.shape[0]
+        if n > self.n_cand:
+            raise ValueError(f"{n} candidates but workspace sized for {self.n_cand}")
+        ph = torch.empty(n, self.Ny, self.Nx, dtype=torch.float32, device=self.device) if phase else None
+        var = torch.empty(n, dtype=torch.float64, device=self.device)
+        L.ssb_reconstruct(self.plan, self.G, ab, self.scratch, ph, var, status=self.status)
+        return ph, var
+
+    def grad(self, aberr: torch.Tensor, grad_phase: torch.Tensor):
+        ab = aberr.to(self.device, torch.float64).reshape(5).contiguous()
+        g = torch.empty(5, dtype=torch.float64, device=self.device)
+        L.ssb_grad(self.plan, self.G, ab, grad_phase.to(torch.float32).contiguous(), g, self.scratch,
+                   status=self.status)
+        return g
+
+    def variance_grad(self, aberr: torch.Tensor, phase: bool = False):
+        ab = aberr.to(self.device, torch.float64).reshape(5).contiguous()
+        var = torch.empty(1, dtype=torch.float64, device=self.device)
+        g = torch.empty(5, dtype=torch.float64, device=self.device)
+        ph = torch.empty(self.Ny, self.Nx, dtype=torch.float32, device=self.device) if phase else None
+        L.ssb_variance_grad(self.plan, self.G, ab, self.scratch, var, g, ph, status=self.status)
+        return var, g, ph
+
+    def trotter_counts(self, rot: float = 0.0):
+        ab = torch.zeros(5, dtype=torch.float64, device=self.device)
+        ab[4] = rot
+        cnt = torch.empty(self.Ny, self.Nx, dtype=torch.int32, device=self.device)
+        L.ssb_trotter_counts(self.plan, ab, cnt, self.scratch)
+        return cnt
+
+    # -- views -----------------------------------------------------------------
+    def G_complex(self) -> torch.Tensor:
+        """G as complex64 [nkx][Ny][P_pad] (K_x >= 0 half)."""
+        nkx, P_pad = self.info["nkx"], self.info["P_pad"]
+        return torch.view_as_complex(self.G.view(nkx, self.Ny, P_pad, 2))
+
+    def check(self, raise_on_error: bool = True) -> int:
+        code = L.status_code(self.status)
+        if code != L.EER4D_OK and raise_on_error:
+            raise L.Eer4dError(code, "device status")
+        return code

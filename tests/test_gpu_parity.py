@@ -1,0 +1,319 @@
+"""GPU (CUDA path through the C ABI) versus the FP64 oracle, element by element.
+
+Tolerances (stated per result): COM sums, PACBED, counts, trotter set sizes:
+bit-exact.  FP32 G: relative max-norm error <= 2e-6 of max|G|.  FP32 SSB phase,
+iDPC phase: relative L2 <= 1e-5.  Variance: relative <= 1e-5.  Adjoint:
+per component <= 1e-4 relative to the largest scaled component.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SCALES = np.array([100.0, 50.0, 50.0, 1.0e4, 0.1])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2104_06336_gb300.buildlib import build
+    build()
+    import paper_2104_06336_gb300 as P
+    P.load()
+    return P
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+class Case:
+    """Events (generated once) + GPU reconstructor + oracle quantities."""
+
+    def __init__(self, w, norm=0, device_gen="cpu", n_cand=1, chunk_frames=None, events=None):
+        import paper_2104_06336_gb300 as P
+        self.w = w
+        self.geom = synth.geometry(w)
+        d = synth.generate(w, device_gen) if events is None else events
+        self.idx_np, self.off_np = d.numpy() if events is None else events.numpy()
+        self.idx = d.idx.to("cuda")
+        self.off = d.off.to("cuda")
+        self.rec = P.Reconstructor(self.geom, norm=norm, n_cand=n_cand)
+        self.rec.load(self.idx, self.off, chunk_frames=chunk_frames)
+        torch.cuda.synchronize()
+        self._G = None
+
+    @property
+    def G_orc(self):
+        if self._G is None:
+            counts = orc.densify(self.idx_np, self.off_np, self.geom)
+            self._G = orc.g_function(counts, self.geom)
+        return self._G
+
+    def G_gpu_full(self):
+        """GPU half spectrum expanded to [P][Ny][Nx] with G(-K) = conj G(K)."""
+        Gh = self.rec.G_complex().cpu().numpy().astype(np.complex128)  # [nkx][Ny][P_pad]
+        P = self.rec.info["P"]
+        Ny, Nx = self.w.scan_ny, self.w.scan_nx
+        out = np.zeros((P, Ny, Nx), dtype=np.complex128)
+        nkx = Nx // 2 + 1
+        out[:, :, :nkx] = np.transpose(Gh[:, :, :P], (2, 1, 0))
+        for mx in range(nkx, Nx):
+            src = out[:, :, Nx - mx]
+            out[:, :, mx] = np.conj(src[:, (-np.arange(Ny)) % Ny])
+        return out
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return Case(synth.workload(1))
+
+
+@pytest.fixture(scope="module")
+def c1_area():
+    return Case(synth.workload(1), norm=1)
+
+
+@pytest.fixture(scope="module")
+def c2small():
+    # detector geometry of the 576x576 workloads (bin 4, 1245 BF pixels) on a
+    # rectangular 48x64 scan: several FFT tiles and ragged pixel tiles
+    return Case(synth.workload(2, scan_ny=48, scan_nx=64), device_gen="cuda")
+
+
+# --------------------------------------------------------------- a1 + a2 ---
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_com_sums_pacbed_bit_exact(which, request):
+    c = request.getfixturevalue(which)
+    import paper_2104_06336_gb300 as P
+    W, H = c.w.det_w, c.w.det_h
+    pac = torch.zeros(W * H, dtype=torch.int64, device="cuda")
+    tot = torch.zeros(3, dtype=torch.int64, device="cuda")
+    P.eer_load_csr(c.rec.plan, c.idx, c.off, pacbed=pac, totals=tot, status=c.rec.status)
+    sums, com, ph = c.rec.com_dpc(c.idx, c.off)
+    torch.cuda.synchronize()
+    sx, sy, n = orc.com_sums(c.idx_np, c.off_np, W, H)
+    np.testing.assert_array_equal(sums.cpu().numpy(), np.stack([sx, sy, n]))
+    np.testing.assert_array_equal(pac.cpu().numpy(), orc.pacbed(c.idx_np, W, H))
+    assert tot.cpu().tolist() == [int(sx.sum()), int(sy.sum()), int(n.sum())]
+    cx, cy = orc.pacbed_centre(sx, sy, n)
+    ox, oy = orc.com_maps(sx, sy, n, cx, cy)
+    assert rel_l2(com.cpu().numpy(), np.stack([ox, oy])) <= 1e-6
+    phi = orc.idpc(ox, oy, c.geom)
+    assert rel_l2(ph.cpu().numpy(), phi) <= 1e-5
+    assert c.rec.check() == 0
+
+
+def test_idpc_regularised(c1):
+    sums, com, ph = c1.rec.com_dpc(c1.idx, c1.off, lam1=0.5, lam2=0.01)
+    sx, sy, n = orc.com_sums(c1.idx_np, c1.off_np, c1.w.det_w, c1.w.det_h)
+    ox, oy = orc.com_maps(sx, sy, n, *orc.pacbed_centre(sx, sy, n))
+    assert rel_l2(ph.cpu().numpy(), orc.idpc(ox, oy, c1.geom, 0.5, 0.01)) <= 1e-5
+
+
+# ------------------------------------------------------------- a4 + a5 -----
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_counts_bit_exact(which, request):
+    c = request.getfixturevalue(which)
+    P_, P_pad = c.rec.info["P"], c.rec.info["P_pad"]
+    counts = c.rec.counts.view(P_pad, -1).float().cpu().numpy()
+    ref = orc.densify(c.idx_np, c.off_np, c.geom)
+    np.testing.assert_array_equal(counts[:P_].astype(np.int64), ref)
+    assert np.all(counts[P_:] == 0)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_g_function_fp32(which, request):
+    c = request.getfixturevalue(which)
+    G = c.G_gpu_full()
+    ref = c.G_orc
+    assert np.abs(G - ref).max() <= 2e-6 * np.abs(ref).max()
+    # DC terms are sums of integers: exact
+    np.testing.assert_array_equal(G[:, 0, 0].real, ref[:, 0, 0].real)
+
+
+def test_chunked_accumulate_equals_single_call(c2small):
+    w = c2small.w
+    import paper_2104_06336_gb300 as P
+    rec = P.Reconstructor(c2small.geom)
+    rec.load(c2small.idx, c2small.off, chunk_frames=3 * w.scan_nx + 5)  # ragged chunks
+    torch.cuda.synchronize()
+    assert torch.equal(rec.G, c2small.rec.G)
+    assert torch.equal(rec.counts, c2small.rec.counts)
+
+
+# ------------------------------------------------------------- trotter -----
+@pytest.mark.parametrize("rot", [0.0, 0.3, -1.1])
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_trotter_set_sizes_bit_exact(which, rot, request):
+    c = request.getfixturevalue(which)
+    cnt = c.rec.trotter_counts(rot).cpu().numpy()
+    P_ = orc.pixel_table(c.geom)["P"]
+    G1 = np.ones((P_, c.w.scan_ny, c.w.scan_nx), dtype=np.complex128)
+    _, nK = orc.ssb_spectrum(G1, c.geom, (0, 0, 0, 0, rot))
+    np.testing.assert_array_equal(cnt, nK)
+
+
+ABERRS = [(0.0, 0.0, 0.0, 0.0, 0.0), (80.0, 15.0, 25.98, 1.0e4, 0.0), (-150.0, 40.0, -30.0, 0.0, 0.2)]
+
+
+@pytest.mark.parametrize("ab", ABERRS)
+@pytest.mark.parametrize("which", ["c1", "c1_area", "c2small"])
+def test_ssb_phase_fp32(which, ab, request):
+    c = request.getfixturevalue(which)
+    norm = "area" if c.rec.plan.norm == 1 else "none"
+    ph, var = c.rec.reconstruct(torch.tensor(ab, dtype=torch.float64))
+    phi, V = orc.ssb_phase(c.G_orc, c.geom, ab, norm)
+    assert rel_l2(ph[0].cpu().numpy(), phi) <= 1e-5
+    assert abs(float(var[0]) - V) <= 1e-5 * V
+    assert c.rec.check() == 0
+
+
+def test_batched_candidates_match_single(c1):
+    import paper_2104_06336_gb300 as P
+    cands = torch.tensor([[80.0, 15.0, 26.0, 1.0e4, 0.1], [0, 0, 0, 0, 0.1], [-200.0, -50.0, 30.0, 0, 0.1],
+                          [10.0, 0, 0, 0, 0.1]], dtype=torch.float64)
+    rec = P.Reconstructor(c1.geom, n_cand=4)
+    rec.load(c1.idx, c1.off)
+    ph, var = rec.reconstruct(cands)
+    for i in range(4):
+        p1, v1 = c1.rec.reconstruct(cands[i])
+        assert torch.equal(ph[i], p1[0])
+        phi, V = orc.ssb_phase(c1.G_orc, c1.geom, cands[i].numpy(), "none")
+        assert rel_l2(ph[i].cpu().numpy(), phi) <= 1e-5
+    # a candidate with a different rotation is flagged, never silently mixed
+    bad = cands.clone()
+    bad[2, 4] = 0.0
+    rec.status.zero_()
+    rec.reconstruct(bad)
+    assert (int(rec.status[0].item()) & P._lib.ST_ROTATION) != 0
+
+
+# --------------------------------------------------------------- adjoint ---
+@pytest.mark.parametrize("which", ["c1", "c1_area", "c2small"])
+def test_adjoint_parity(which, request):
+    c = request.getfixturevalue(which)
+    norm = "area" if c.rec.plan.norm == 1 else "none"
+    theta = np.array([50.0, 10.0, -20.0, 2.0e3, 0.05])
+    u = np.random.default_rng(5).normal(size=(c.w.scan_ny, c.w.scan_nx)).astype(np.float32)
+    g = c.rec.grad(torch.tensor(theta), torch.from_numpy(u).cuda()).cpu().numpy()
+    ref = orc.ssb_grad(c.G_orc, c.geom, theta, u.astype(np.float64), norm)
+    tol = 1e-4 * np.max(np.abs(ref) * SCALES) / SCALES
+    assert np.all(np.abs(g - ref) <= tol + 1e-4 * np.abs(ref)), (g, ref)
+    V, gv, ph = c.rec.variance_grad(torch.tensor(theta), phase=True)
+    Vr, gr, phr = orc.ssb_value_and_grad_var(c.G_orc, c.geom, theta, norm)
+    assert abs(float(V) - Vr) <= 1e-5 * Vr
+    tol = 1e-4 * np.max(np.abs(gr) * SCALES) / SCALES
+    assert np.all(np.abs(gv.cpu().numpy() - gr) <= tol + 1e-4 * np.abs(gr)), (gv, gr)
+    assert rel_l2(ph.cpu().numpy(), phr) <= 1e-5
+
+
+def test_autograd_function(c1):
+    import paper_2104_06336_gb300 as P
+    theta = torch.tensor([30.0, 5.0, -5.0, 0.0, 0.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    phi = P.ssb_phase(theta, c1.rec)
+    loss = (phi.double() ** 2).mean()
+    loss.backward()
+    g_ref = c1.rec.grad(theta.detach(), (2 * phi.detach() / phi.numel()).float())
+    assert torch.allclose(theta.grad, g_ref, rtol=1e-6, atol=0)
+
+
+# ------------------------------------------------------------ edge cases ---
+def _custom(w, idx, off):
+    import paper_2104_06336_gb300 as P
+    rec = P.Reconstructor(synth.geometry(w))
+    i = torch.tensor(np.asarray(idx, dtype=np.uint32).view(np.int32), device="cuda")
+    o = torch.tensor(np.asarray(off, dtype=np.int64), device="cuda")
+    return rec, i, o
+
+
+def test_empty_and_out_of_range_events():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(1, scan_ny=4, scan_nx=4)
+    # frames: empty, valid, one bad index (dropped), empty ...
+    idx = [2080, 2081, 4096 + 7, 2080] + [2079] * 3
+    off = [0, 0, 2, 3, 4] + [7] * 12
+    rec, i, o = _custom(w, idx, off)
+    rec.load(i, o)
+    sums, com, ph = rec.com_dpc(i, o)
+    torch.cuda.synchronize()
+    idx_np = np.array(idx, dtype=np.uint32)
+    off_np = np.array(off, dtype=np.uint64)
+    sx, sy, n = orc.com_sums(idx_np, off_np, 64, 64)
+    np.testing.assert_array_equal(sums.cpu().numpy(), np.stack([sx, sy, n]))
+    assert com[:, 0].abs().sum().item() == 0.0  # empty frame -> COM 0
+    st = rec.status.cpu().numpy()
+    assert st[0] & P._lib.ST_RANGE and st[1] >= 1
+    counts = rec.counts.view(rec.info["P_pad"], -1).float().cpu().numpy()
+    np.testing.assert_array_equal(counts[:rec.info["P"]], orc.densify(idx_np, off_np, synth.geometry(w)))
+
+
+def test_all_empty_dataset_gives_zero_phase():
+    w = synth.workload(1, scan_ny=4, scan_nx=4)
+    rec, i, o = _custom(w, [], [0] * 17)
+    rec.load(i, o)
+    ph, var = rec.reconstruct(torch.zeros(5, dtype=torch.float64))
+    assert ph.abs().max().item() == 0.0 and var.item() == 0.0
+    assert rec.check() == 0
+
+
+def test_corrupt_offsets_flagged_without_fault():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(1, scan_ny=4, scan_nx=4)
+    idx = [2080] * 10
+    off = [0, 5, 3, 10**12, 8] + [10] * 12   # decreasing and beyond the array
+    rec, i, o = _custom(w, idx, off)
+    rec.load(i, o)
+    rec.com_dpc(i, o)
+    torch.cuda.synchronize()
+    assert int(rec.status[0].item()) & P._lib.ST_OFFSETS
+    assert rec.check(raise_on_error=False) == P._lib.EER4D_EOFFSETS
+
+
+def test_pixel_overflow_flagged():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(1, scan_ny=2, scan_nx=2)
+    idx = [2080] * 2100 + [2081]
+    off = [0, 2101, 2101, 2101, 2101]
+    rec, i, o = _custom(w, idx, off)
+    rec.load(i, o)
+    torch.cuda.synchronize()
+    assert int(rec.status[0].item()) & P._lib.ST_OVERFLOW
+
+
+def test_out_of_order_chunks_rejected(c1):
+    import paper_2104_06336_gb300 as P
+    with pytest.raises(P.Eer4dError) as e:
+        P.ssb_accumulate(c1.rec.plan, c1.idx, c1.off[64:129], 64, c1.rec.counts, c1.rec.G, False)
+    assert e.value.code == P._lib.EER4D_EORDER
+
+
+# ------------------------------------------------- precision workload size --
+@pytest.fixture(scope="module")
+def c2full():
+    return Case(synth.workload(2), device_gen="cuda")
+
+
+def test_precision_workload_full_size(c2full):
+    """256x256 scan, 576x576 detector binned 4x, 1245 BF pixels: counts exact,
+    FP32 G and SSB phase against the FP64 oracle."""
+    c = c2full
+    P_, P_pad = c.rec.info["P"], c.rec.info["P_pad"]
+    assert P_ == 1245
+    counts = c.rec.counts.view(P_pad, -1).float().cpu().numpy()[:P_].astype(np.int64)
+    ref = orc.densify(c.idx_np, c.off_np, c.geom)
+    np.testing.assert_array_equal(counts, ref)
+    G = c.G_orc
+    ph, var = c.rec.reconstruct(torch.zeros(5, dtype=torch.float64))
+    phi, V = orc.ssb_phase(G, c.geom, (0, 0, 0, 0, 0), "none")
+    err = rel_l2(ph[0].cpu().numpy(), phi)
+    print(f"precision workload FP32 SSB rel L2 = {err:.3e}")
+    assert err <= 1e-5
