@@ -166,9 +166,13 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
         lut2[(size_t)v * g.pw + u] = idx;
         pix.push_back(make_short2((short)kx, (short)ky));
         if ((float)(kx * kx + ky * ky) < k0sq) {
-          if (lo > hi) { lo = kx; plo = idx; }
-          if (kx != hi + 1 && hi >= lo) { free_plan(p); return EER4D_EINVAL; }
-          hi = kx;
+          if (lo > hi) {
+            lo = hi = kx;
+            plo = idx;
+          } else {
+            if (kx != hi + 1) { free_plan(p); return EER4D_EINVAL; }  // BF row not contiguous
+            hi = kx;
+          }
           ++P_bf;
         }
       }

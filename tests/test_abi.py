@@ -67,3 +67,21 @@ def test_invalid_geometry_rejected_before_any_cuda_call(lib):
     assert lib.eer4d_plan_create(ctypes.byref(g), 0, 0, ctypes.byref(h)) == -1  # odd scan
     g.scan_nx = 32
     assert lib.eer4d_plan_create(ctypes.byref(g), 7, 0, ctypes.byref(h)) == -1  # precision
+
+
+def test_valid_geometries_pass_host_validation(lib):
+    """Every workload geometry passes the host checks: plan creation fails only
+    for want of a GPU here (ECUDA), or succeeds on a GPU machine."""
+    import synth
+    from paper_2104_06336_gb300._lib import Geom
+    lib.eer4d_plan_create.argtypes = [ctypes.POINTER(Geom), ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p)]
+    lib.eer4d_plan_destroy.argtypes = [ctypes.c_void_p]
+    for cfg in (1, 2, 3, 4, 5):
+        g = synth.geometry(synth.workload(cfg))
+        G = Geom(**{k: g[k] for k, _ in Geom._fields_})
+        h = ctypes.c_void_p()
+        rc = lib.eer4d_plan_create(ctypes.byref(G), 0, 0, ctypes.byref(h))
+        assert rc in (0, -6), (cfg, rc)
+        if rc == 0:
+            lib.eer4d_plan_destroy(h)
