@@ -238,6 +238,10 @@ def run_ours(args, rank, world, local_rank):
     nst = len(P._lib.STAGES)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(nst)] for _ in range(args.steps)]
+    for row in ev:  # torch creates CUDA events lazily: record once so the handles exist
+        for a, b in row:
+            a.record()
+            b.record()
     for _ in range(args.warmup):
         step(idx, off)
     torch.cuda.synchronize()
