@@ -48,6 +48,7 @@ extern "C" {
 #define EER4D_ECUDA     -6  /* a CUDA call failed */
 #define EER4D_ENOMEM    -7  /* plan tables could not be allocated */
 #define EER4D_EORDER    -8  /* ssb_accumulate chunks not delivered in frame order */
+#define EER4D_ESCRATCH  -9  /* plan needs more than the static scratch of ssb_reconstruct_static */
 
 /* ---- device status bits (d_status[0]) ---------------------------------- */
 #define EER4D_ST_RANGE    0x01u
@@ -200,6 +201,26 @@ int ssb_trotter_counts(const eer4d_plan* plan, const double* d_aberr, int32_t* d
 int ssb_refocus_step(const eer4d_plan* plan, const void* d_G, double* d_aberr, const double* d_step,
                      void* d_scratch, float* d_phase, double* d_var, double* d_grad,
                      uint32_t* d_status, void* stream);
+
+/* ---- reconstruction without scratch allocation --------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory where they want an image (a host application
+ * that owns every device buffer, or a real-time acquisition loop that must
+ * not call cudaMalloc because it can synchronise the device).
+ * ssb_reconstruct_static computes what ssb_reconstruct computes for ONE
+ * candidate (d_aberr: double[5]; d_phase: float [F], nullable; d_var: double
+ * [1], nullable) but takes no scratch argument and allocates nothing: its
+ * working memory is a static device array of EER4D_STATIC_SCRATCH_BYTES
+ * (8 MiB) inside the library, held by every GPU that loads the library until
+ * the process exits.  A plan needing more (scans beyond about 1024x1024)
+ * returns EER4D_ESCRATCH with nothing enqueued.  All calls on a device share
+ * the array, which keeps the last call's contents (nothing in it needs to
+ * start at zero); calls that overlap on the GPU race on it, so order them on
+ * one stream.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture. */
+#define EER4D_STATIC_SCRATCH_BYTES (8u << 20)
+int ssb_reconstruct_static(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
+                           float* d_phase, double* d_var, uint32_t* d_status, void* stream);
 
 /* ---- measurement hooks (not part of the method) ------------------------------
  * Stage ids for eer4d_set_stage_events. */

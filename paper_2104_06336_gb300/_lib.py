@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_PKG, "libeer4d.so")
 
 EER4D_OK, EER4D_EINVAL, EER4D_ERANGE, EER4D_EOFFSETS = 0, -1, -2, -3
 EER4D_EOVERFLOW, EER4D_ETIMEOUT, EER4D_ECUDA, EER4D_ENOMEM, EER4D_EORDER = -4, -5, -6, -7, -8
+EER4D_ESCRATCH = -9
+STATIC_SCRATCH_BYTES = 8 << 20
 ST_RANGE, ST_OFFSETS, ST_OVERFLOW, ST_TIMEOUT, ST_ROTATION = 0x1, 0x2, 0x4, 0x8, 0x10
 FP32_FFT, SPLIT_FP16 = 0, 1
 NORM_NONE, NORM_AREA = 0, 1
@@ -25,7 +27,7 @@ EXPORTS = [
     "eer4d_plan_create", "eer4d_plan_destroy", "eer4d_plan_info", "eer4d_workspace_bytes",
     "eer4d_status_code", "eer4d_strerror", "eer4d_last_error", "eer_load_csr", "com_dpc",
     "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
-    "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count",
+    "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
 ]
 STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image"]
 
@@ -89,6 +91,7 @@ def load(path: str | None = None):
         "ssb_refocus_step": (I32, [P, P, P, P, P, P, P, P, P, P]),
         "eer4d_set_stage_events": (I32, [P, P, P]),
         "eer4d_launch_count": (C.c_uint64, []),
+        "ssb_reconstruct_static": (I32, [P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -229,3 +232,11 @@ def eer4d_set_stage_events(plan: Plan, starts=None, stops=None):
 
 def eer4d_launch_count() -> int:
     return int(load().eer4d_launch_count())
+
+
+def ssb_reconstruct_static(plan: Plan, G, aberr, phase=None, var=None, status=None):
+    """One-candidate ssb_reconstruct whose working memory is the library's
+    static device array (no scratch argument, no allocation)."""
+    _check(load().ssb_reconstruct_static(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
+                                         _ptr(phase, "phase"), _ptr(var, "var"),
+                                         _ptr(status, "status"), _stream()), "ssb_reconstruct_static")

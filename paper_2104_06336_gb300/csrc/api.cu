@@ -266,6 +266,7 @@ const char* eer4d_strerror(int code) {
     case EER4D_ECUDA: return "CUDA error";
     case EER4D_ENOMEM: return "out of memory";
     case EER4D_EORDER: return "chunks not delivered in frame order";
+    case EER4D_ESCRATCH: return "plan needs more scratch than the 8 MiB static array of ssb_reconstruct_static";
     default: return "unknown error";
   }
 }
