@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=5)
+    ap.add_argument("--scan", type=int, default=0, help="smaller square scan of the same geometry (profiling)")
     ap.add_argument("--refocus-steps", type=int, default=220)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -213,7 +214,8 @@ def run_ours(args, rank, world, local_rank):
     P.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.workload(args.workload, seed=synth.workload(args.workload).seed + 1000 * rank)
+    over = dict(scan_ny=args.scan, scan_nx=args.scan) if args.scan else {}
+    w = synth.workload(args.workload, seed=synth.workload(args.workload).seed + 1000 * rank, **over)
     geom = synth.geometry(w)
     d = synth.generate(w, dev)
     idx, off = d.idx.contiguous(), d.off.contiguous()

@@ -4,6 +4,7 @@
 // COM field (Sec. V).  All are batched Stockham FFTs in shared memory
 // (fft.cuh); real data use the two-real-rows-in-one-complex-transform form.
 #include "fft.cuh"
+#include "fft_reg.cuh"
 
 namespace {
 
@@ -210,12 +211,89 @@ cudaError_t cols(const FftDesc& d, const float2* in, float2* out, int dir, int n
   return cudaGetLastError();
 }
 
+// ---- register four-step dispatch (power-of-two N in [16, 1024]) ----------
+bool reg_size(int N) { return N >= 16 && N <= 1024 && (N & (N - 1)) == 0; }
+
+template <int R1, int R2, int CB, int DIR>
+cudaError_t cols_reg_t(const FftDesc& d, const float2* in, float2* out, int ncols, int ld_in,
+                       int ld_out, long long bs_in, long long bs_out, int nbatch, float scale,
+                       cudaStream_t s) {
+  constexpr int NT = (R1 > R2 ? R1 : R2) * CB;
+  const size_t sm = sizeof(float2) * (size_t)R1 * CB * (R2 + 1);
+  auto kern = k_colfft_reg<R1, R2, CB, DIR>;
+  cudaError_t e = set_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((ncols + CB - 1) / CB, nbatch);
+  kern<<<grid, NT, sm, s>>>(in, out, d.tw, ncols, ld_in, ld_out, bs_in, bs_out, scale);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int DIR>
+cudaError_t cols_reg(const FftDesc& d, const float2* in, float2* out, int ncols, int ld_in,
+                     int ld_out, long long bs_in, long long bs_out, int nbatch, float scale,
+                     cudaStream_t s) {
+#define EER4D_COLS(R1, R2, CB) \
+  return cols_reg_t<R1, R2, CB, DIR>(d, in, out, ncols, ld_in, ld_out, bs_in, bs_out, nbatch, scale, s)
+  switch (d.N) {
+    case 1024: EER4D_COLS(32, 32, 8);
+    case 512: EER4D_COLS(32, 16, 8);
+    case 256: EER4D_COLS(16, 16, 16);
+    case 128: EER4D_COLS(16, 8, 16);
+    case 64: EER4D_COLS(8, 8, 32);
+    case 32: EER4D_COLS(8, 4, 32);
+    default: EER4D_COLS(4, 4, 64);
+  }
+#undef EER4D_COLS
+}
+
+template <int R1, int R2, int CP>
+cudaError_t r2c_reg_t(const FftDesc& d, const __half* in, float2* out, int nA, int c0, int nc,
+                      long long in_sa, long long in_sc, long long out_skx, long long out_sa,
+                      long long out_sc, cudaStream_t s) {
+  constexpr int N = R1 * R2;
+  const size_t a = (size_t)R1 * CP * (R2 + 1), b = (size_t)N * CP;
+  const size_t sm = sizeof(float2) * (a > b ? a : b);
+  auto kern = k_rowfft_r2c_reg<R1, R2, CP>;
+  cudaError_t e = set_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nA + 2 * CP - 1) / (2 * CP), nc);
+  kern<<<grid, R1 * CP, sm, s>>>(in, out, d.tw, nA, c0, in_sa, in_sc, out_skx, out_sa, out_sc);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t r2c_reg(const FftDesc& d, const __half* in, float2* out, int nA, int c0, int nc,
+                    long long in_sa, long long in_sc, long long out_skx, long long out_sa,
+                    long long out_sc, cudaStream_t s) {
+#define EER4D_R2C(R1, R2, CP) \
+  return r2c_reg_t<R1, R2, CP>(d, in, out, nA, c0, nc, in_sa, in_sc, out_skx, out_sa, out_sc, s)
+  switch (d.N) {
+    case 1024: EER4D_R2C(32, 32, 8);
+    case 512: EER4D_R2C(32, 16, 8);
+    case 256: EER4D_R2C(16, 16, 16);
+    case 128: EER4D_R2C(16, 8, 16);
+    case 64: EER4D_R2C(8, 8, 32);
+    case 32: EER4D_R2C(8, 4, 32);
+    default: EER4D_R2C(4, 4, 64);
+  }
+#undef EER4D_R2C
+}
+
 }  // namespace
 
 cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
                           cudaStream_t s) {
   if (y1 <= y0) return cudaSuccess;
   const FftDesc& d = p->fx;
+  const long long NRl = (long long)p->g.scan_ny * p->g.scan_nx;
+  if (reg_size(d.N)) {
+    stage_begin(p, EER4D_STAGE_DFT_X, s);
+    cudaError_t e = r2c_reg(d, counts, G, p->P_pad, y0, y1 - y0, NRl, (long long)p->g.scan_nx,
+                            (long long)p->g.scan_ny * p->P_pad, 1, (long long)p->P_pad, s);
+    stage_end(p, EER4D_STAGE_DFT_X, s);
+    return e;
+  }
   const int nb = rows_nb(d.N);
   const int TA = 2 * nb;
   const size_t sm = (size_t)2 * nb * d.N * sizeof(float2);
@@ -235,7 +313,9 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
 cudaError_t launch_stage2(const eer4d_plan* p, float2* G, cudaStream_t s) {
   const long long bs = (long long)p->g.scan_ny * p->P_pad;
   stage_begin(p, EER4D_STAGE_DFT_Y, s);
-  cudaError_t e = cols(p->fy, G, G, 1, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx, 1.f, s);
+  cudaError_t e = reg_size(p->fy.N)
+                      ? cols_reg<1>(p->fy, G, G, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx, 1.f, s)
+                      : cols(p->fy, G, G, 1, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx, 1.f, s);
   stage_end(p, EER4D_STAGE_DFT_Y, s);
   return e;
 }
@@ -244,7 +324,8 @@ cudaError_t launch_c2r_image(const eer4d_plan* p, float2* H, float* phase, int n
                              cudaStream_t s) {
   const int Ny = p->g.scan_ny, Nx = p->g.scan_nx, nkx = p->nkx;
   const long long bs = (long long)Ny * nkx;
-  cudaError_t e = cols(p->fy, H, H, -1, nkx, nkx, nkx, bs, bs, n_cand, 1.f, s);
+  cudaError_t e = reg_size(p->fy.N) ? cols_reg<-1>(p->fy, H, H, nkx, nkx, nkx, bs, bs, n_cand, 1.f, s)
+                                    : cols(p->fy, H, H, -1, nkx, nkx, nkx, bs, bs, n_cand, 1.f, s);
   if (e != cudaSuccess) return e;
   const FftDesc& d = p->fx;
   const int nb = rows_nb(d.N), TA = 2 * nb;

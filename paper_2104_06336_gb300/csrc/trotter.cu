@@ -357,20 +357,37 @@ __global__ void k_reduce_partials(const double* partial, int nblk, int nv, doubl
   }
 }
 
-// V_c = sum_b w(b) |H_c(b)|^2 / N_R^2 over the stored half (block per candidate).
-__global__ void k_variance(const float2* __restrict__ H, int Ny, int nkx, int Nx, double NR,
-                           double* var) {
+// V_c = sum_b w(b) |H_c(b)|^2 / N_R^2 over the stored half: per-block partial
+// sums (grid kVarBlocks x n_cand), then a fixed-order final sum per candidate.
+constexpr int kVarBlocks = 128;
+
+__global__ void k_variance_partial(const float2* __restrict__ H, int Ny, int nkx, int Nx,
+                                   double* part) {
   __shared__ double red[256];
-  const int c = blockIdx.x;
+  const int c = blockIdx.y;
   const float2* h = H + (size_t)c * Ny * nkx;
   double s = 0.0;
   const int n = Ny * nkx;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int mx = i % nkx;
     const double w = (mx == 0 || 2 * mx == Nx) ? 1.0 : 2.0;
     const float2 v = h[i];
     s += w * ((double)v.x * v.x + (double)v.y * v.y);
   }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_variance_final(const double* __restrict__ part, int nblk, double NR, double* var) {
+  __shared__ double red[128];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)c * nblk + b];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -394,7 +411,7 @@ int trot_blocks(const eer4d_plan* p) {
 }
 
 struct Layout {
-  size_t coef, ek, gscale, H, partial, total;
+  size_t coef, ek, gscale, H, partial, vpart, total;
 };
 Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   Layout L;
@@ -405,6 +422,7 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   const int nh = (mode == TROT_GRAD || mode == TROT_COUNT) ? 0 : n_cand;
   L.H = o; o = align256(o + sizeof(float2) * (size_t)nh * p->g.scan_ny * p->nkx);
   L.partial = o; o = align256(o + sizeof(double) * 5 * trot_blocks(p));
+  L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)nh);
   L.total = o;
   return L;
 }
@@ -432,6 +450,7 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   double* gsc = reinterpret_cast<double*>(sb + L.gscale);
   float2* H = reinterpret_cast<float2*>(sb + L.H);
   double* partial = reinterpret_cast<double*>(sb + L.partial);
+  double* vpart = reinterpret_cast<double*>(sb + L.vpart);
   cudaError_t e;
   stage_begin(p, EER4D_STAGE_TROTTER, s);
   k_prep<<<n_cand, 256, 0, s>>>(aberr, n_cand, p->d_pix, p->P_pad, p->P, p->g.dalpha_rad,
@@ -476,8 +495,10 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   const int nc = mode == TROT_FWD ? n_cand : 1;
   stage_begin(p, EER4D_STAGE_IMAGE, s);
   if (var_out) {
-    k_variance<<<nc, 256, 0, s>>>(H, p->g.scan_ny, p->nkx, p->g.scan_nx, (double)p->F, var_out);
-    count_launches(1);
+    k_variance_partial<<<dim3(kVarBlocks, nc), 256, 0, s>>>(H, p->g.scan_ny, p->nkx, p->g.scan_nx,
+                                                             vpart);
+    k_variance_final<<<nc, 128, 0, s>>>(vpart, kVarBlocks, (double)p->F, var_out);
+    count_launches(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (phase_out && (e = launch_c2r_image(p, H, phase_out, nc, s)) != cudaSuccess) return e;
