@@ -183,7 +183,7 @@ STAGE_BYTES_DOC = {
     "dpc": "8 B/frame in + 4 B/frame out",
     "scatter": "4 B/event + 8 B/frame in; 2 B x P_pad per frame out",
     "dft_x": "2 B x P_pad per frame in; 8 B x P_pad x (Nx/2+1)/Nx per frame out",
-    "dft_y": "8 B x P_pad x (Nx/2+1)/Nx per frame in and out",
+    "dft_y": "8 B x P_pad x (Nx/2+1)/Nx per frame in and out (transposed out)",
     "trotter": "8 B per (pixel, K) pair of the trotter sets + 8 B per stored bin out",
     "image": "8 B per stored bin in (x2) + 4 B/frame out",
 }
@@ -234,7 +234,7 @@ def run_ours(args, rank, world, local_rank):
         P.eer_load_csr(rec.plan, ix, of, totals=rec.totals, status=rec.status)
         P.com_dpc(rec.plan, ix, of, sums, com, dpc, totals=rec.totals, scratch=rec.scratch,
                   status=rec.status)
-        P.ssb_accumulate(rec.plan, ix, of, 0, rec.counts, rec.G, True, status=rec.status)
+        P.ssb_accumulate(rec.plan, ix, of, 0, rec.work, rec.G, True, status=rec.status)
         P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var, status=rec.status)
 
     nst = len(P._lib.STAGES)

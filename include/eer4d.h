@@ -114,9 +114,10 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
 void eer4d_plan_destroy(eer4d_plan* plan);
 int eer4d_plan_info(const eer4d_plan* plan, eer4d_info* h_info);
 
-/* Bytes the caller allocates: counts (ssb_accumulate), G (the resident
- * spectrum) and scratch (the largest need of com_dpc, ssb_reconstruct with
- * n_cand candidates, ssb_grad and ssb_variance_grad). */
+/* Bytes the caller allocates: counts (the accumulation workspace of
+ * ssb_accumulate), G (the resident spectrum) and scratch (the largest need of
+ * com_dpc, ssb_reconstruct with n_cand candidates, ssb_grad and
+ * ssb_variance_grad). */
 int eer4d_workspace_bytes(const eer4d_plan* plan, int n_cand, size_t* counts_bytes,
                           size_t* G_bytes, size_t* scratch_bytes);
 
@@ -148,13 +149,15 @@ int com_dpc(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const
             double cy, double lam1, double lam2, void* d_scratch, uint32_t* d_status, void* stream);
 
 /* ---- a4 + a5: bin/crop/densify and the G function (Table 1; Sec. IV) -------
- * Scatters frames [first_frame, first_frame + n_frames) into d_counts
- * (fp16 [P_pad][scan_ny*scan_nx], exact integers up to 2048), then runs the
- * scan-axis DFT along x for every scan row completed by this chunk.  Chunks
+ * Scatters frames [first_frame, first_frame + n_frames) into the counts at
+ * the start of the workspace d_counts (fp16 [P_pad][scan_ny*scan_nx], exact
+ * integers up to 2048), then runs the scan-axis DFT along x for every scan
+ * row completed by this chunk into the second part of the workspace (at the
+ * next 256-byte boundary: complex64 [scan_nx/2+1][scan_ny][P_pad]).  Chunks
  * must arrive in frame order starting at frame 0 (else EORDER).  With
  * is_last (the chunk ends at the last frame) the DFT along y completes
- * G(k, K) = F_{R->K} counts in d_G: complex64 [scan_nx/2+1][scan_ny][P_pad]
- * (K_x >= 0 half; G(k,-K) = conj G(k,K)), pixel innermost. */
+ * G(k, K) = F_{R->K} counts in d_G: complex64 [scan_nx/2+1][P_pad][scan_ny]
+ * (K_x >= 0 half, K_y innermost; G(k,-K) = conj G(k,K)). */
 int ssb_accumulate(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
                    uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
                    int is_last, uint32_t* d_status, void* stream);

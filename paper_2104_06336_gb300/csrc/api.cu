@@ -86,13 +86,21 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_luty);
   cudaFree(p->d_lut2);
   cudaFree(p->d_pix);
+  cudaFree(p->d_bfp);
   cudaFree(p->d_rows);
   cudaFree(p->d_tw_y);
   cudaFree(p->d_tw_x);
   free(p);
 }
 
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 }  // namespace
+
+size_t work_counts_bytes(const eer4d_plan* p) { return (size_t)2 * p->P_pad * p->F; }
+size_t work_bytes(const eer4d_plan* p) {
+  return al256(work_counts_bytes(p)) + sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
+}
 
 void stage_begin(const eer4d_plan* p, int stage, cudaStream_t s) {
   if (p && p->ev_start[stage]) cudaEventRecord(p->ev_start[stage], s);
@@ -186,6 +194,9 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   p->n_rows = (int)rows.size();
   p->list_max = (P_bf + 1) & ~1;
   pix.resize(p->P_pad, make_short2(0, 0));
+  std::vector<int32_t> bfp;  // kept-pixel index of every bright-field pixel, row-major
+  for (const int4& R : rows)
+    for (int kx = R.y; kx <= R.z; ++kx) bfp.push_back(R.w + (kx - R.y));
 
   std::vector<int16_t> lutx(g.det_w), luty(g.det_h);
   for (uint32_t x = 0; x < g.det_w; ++x) {
@@ -201,6 +212,7 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   cudaError_t e;
   if ((e = upload(&p->d_lutx, lutx)) != cudaSuccess || (e = upload(&p->d_luty, luty)) != cudaSuccess ||
       (e = upload(&p->d_lut2, lut2)) != cudaSuccess || (e = upload(&p->d_pix, pix)) != cudaSuccess ||
+      (e = upload(&p->d_bfp, bfp)) != cudaSuccess ||
       (e = upload(&p->d_rows, rows)) != cudaSuccess ||
       (e = make_fft((int)g.scan_ny, p->fy, &p->d_tw_y)) != cudaSuccess ||
       (e = make_fft((int)g.scan_nx, p->fx, &p->d_tw_x)) != cudaSuccess) {
@@ -229,7 +241,7 @@ int eer4d_plan_info(const eer4d_plan* p, eer4d_info* info) {
 int eer4d_workspace_bytes(const eer4d_plan* p, int n_cand, size_t* counts_bytes, size_t* G_bytes,
                           size_t* scratch_bytes) {
   if (!p || n_cand < 1 || n_cand > 1024) return EER4D_EINVAL;
-  if (counts_bytes) *counts_bytes = (size_t)2 * p->P_pad * p->F;
+  if (counts_bytes) *counts_bytes = work_bytes(p);
   if (G_bytes) *G_bytes = sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
   if (scratch_bytes) {
     size_t s = sizeof(float2) * (size_t)p->F;  // com_dpc
@@ -306,16 +318,18 @@ int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
   if (first_frame != p->next_frame) return EER4D_EORDER;
   cudaStream_t s = (cudaStream_t)stream;
   __half* counts = static_cast<__half*>(d_counts);
+  float2* X1 = reinterpret_cast<float2*>(static_cast<unsigned char*>(d_counts) +
+                                         al256(work_counts_bytes(p)));
   float2* G = static_cast<float2*>(d_G);
   int rc = cuda_fail(launch_scatter(p, d_idx, n_idx, d_off, first_frame, n_frames, counts,
                                     d_status, s));
   if (rc != EER4D_OK) return rc;
   const uint64_t Nx = p->g.scan_nx;
-  rc = cuda_fail(launch_stage1(p, counts, G, (int)(first_frame / Nx), (int)(end / Nx), s));
+  rc = cuda_fail(launch_stage1(p, counts, X1, (int)(first_frame / Nx), (int)(end / Nx), s));
   if (rc != EER4D_OK) return rc;
   p->next_frame = end;
   if (is_last) {
-    rc = cuda_fail(launch_stage2(p, G, s));
+    rc = cuda_fail(launch_stage2(p, X1, G, s));
     p->next_frame = 0;
   }
   return rc;

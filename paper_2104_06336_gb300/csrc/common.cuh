@@ -61,6 +61,7 @@ struct eer4d_plan {
   int16_t* d_luty;           // [det_h] binned v or -1
   int32_t* d_lut2;           // [ph*pw] kept pixel index or -1
   short2* d_pix;             // [P_pad] (kx, ky)
+  int32_t* d_bfp;            // [P_bf] kept-pixel index of each bright-field pixel (row-major)
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
   float2* d_tw_y;            // [scan_ny]
   float2* d_tw_x;            // [scan_nx]
@@ -129,7 +130,13 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
                            uint32_t* st, cudaStream_t s);
 cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
                           cudaStream_t s);
-cudaError_t launch_stage2(const eer4d_plan* p, float2* G, cudaStream_t s);
+cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cudaStream_t s);
+cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, int batch,
+                             cudaStream_t s);
+// accumulation workspace of ssb_accumulate: fp16 counts [P_pad][F], then (at a
+// 256-byte boundary) the DFT-along-x intermediate complex64 [nkx][Ny][P_pad]
+size_t work_counts_bytes(const eer4d_plan* p);
+size_t work_bytes(const eer4d_plan* p);
 cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam1, double lam2,
                         cudaStream_t s);
 cudaError_t launch_c2r_image(const eer4d_plan* p, float2* H, float* phase, int n_cand, cudaStream_t s);

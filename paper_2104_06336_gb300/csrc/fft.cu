@@ -181,6 +181,25 @@ __global__ void k_idpc_filter(float2* Z, int Ny, int Nx, float inv_lx, float inv
   }
 }
 
+// out[b][c][r] = in[b][r][c] for a batch of [rows][cols] complex matrices
+__global__ void k_transpose(const float2* __restrict__ in, float2* __restrict__ out, int rows,
+                            int cols) {
+  __shared__ float2 t[32][33];
+  const size_t b = blockIdx.z;
+  in += b * (size_t)rows * cols;
+  out += b * (size_t)rows * cols;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
 int cols_nb(int N) {
   int nb = 16;
   while (nb > 1 && (size_t)2 * nb * N * sizeof(float2) > 96 * 1024) nb >>= 1;
@@ -214,13 +233,13 @@ cudaError_t cols(const FftDesc& d, const float2* in, float2* out, int dir, int n
 // ---- register four-step dispatch (power-of-two N in [16, 1024]) ----------
 bool reg_size(int N) { return N >= 16 && N <= 1024 && (N & (N - 1)) == 0; }
 
-template <int R1, int R2, int CB, int DIR>
+template <int R1, int R2, int CB, int DIR, bool TOUT>
 cudaError_t cols_reg_t(const FftDesc& d, const float2* in, float2* out, int ncols, int ld_in,
                        int ld_out, long long bs_in, long long bs_out, int nbatch, float scale,
                        cudaStream_t s) {
   constexpr int NT = (R1 > R2 ? R1 : R2) * CB;
-  const size_t sm = sizeof(float2) * (size_t)R1 * CB * (R2 + 1);
-  auto kern = k_colfft_reg<R1, R2, CB, DIR>;
+  const size_t sm = sizeof(float2) * ((size_t)R1 * CB * (R2 + 1) + 2 * CB);
+  auto kern = k_colfft_reg<R1, R2, CB, DIR, TOUT>;
   cudaError_t e = set_smem(kern, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((ncols + CB - 1) / CB, nbatch);
@@ -229,12 +248,12 @@ cudaError_t cols_reg_t(const FftDesc& d, const float2* in, float2* out, int ncol
   return cudaGetLastError();
 }
 
-template <int DIR>
+template <int DIR, bool TOUT = false>
 cudaError_t cols_reg(const FftDesc& d, const float2* in, float2* out, int ncols, int ld_in,
                      int ld_out, long long bs_in, long long bs_out, int nbatch, float scale,
                      cudaStream_t s) {
 #define EER4D_COLS(R1, R2, CB) \
-  return cols_reg_t<R1, R2, CB, DIR>(d, in, out, ncols, ld_in, ld_out, bs_in, bs_out, nbatch, scale, s)
+  return cols_reg_t<R1, R2, CB, DIR, TOUT>(d, in, out, ncols, ld_in, ld_out, bs_in, bs_out, nbatch, scale, s)
   switch (d.N) {
     case 1024: EER4D_COLS(32, 32, 8);
     case 512: EER4D_COLS(32, 16, 8);
@@ -282,6 +301,14 @@ cudaError_t r2c_reg(const FftDesc& d, const __half* in, float2* out, int nA, int
 
 }  // namespace
 
+cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, int batch,
+                             cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
                           cudaStream_t s) {
   if (y1 <= y0) return cudaSuccess;
@@ -310,12 +337,19 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage2(const eer4d_plan* p, float2* G, cudaStream_t s) {
-  const long long bs = (long long)p->g.scan_ny * p->P_pad;
+cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cudaStream_t s) {
+  const int Ny = p->g.scan_ny;
+  const long long bs = (long long)Ny * p->P_pad;
   stage_begin(p, EER4D_STAGE_DFT_Y, s);
-  cudaError_t e = reg_size(p->fy.N)
-                      ? cols_reg<1>(p->fy, G, G, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx, 1.f, s)
-                      : cols(p->fy, G, G, 1, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx, 1.f, s);
+  cudaError_t e;
+  if (reg_size(p->fy.N)) {
+    e = cols_reg<1, true>(p->fy, X1, G, p->P_pad, p->P_pad, Ny, bs, bs, p->nkx, 1.f, s);
+  } else {
+    // generic lengths: in-place column FFT, then a tiled transpose into G
+    e = cols(p->fy, X1, const_cast<float2*>(X1), 1, p->P_pad, p->P_pad, p->P_pad, bs, bs, p->nkx,
+             1.f, s);
+    if (e == cudaSuccess) e = launch_transpose(X1, G, Ny, p->P_pad, p->nkx, s);
+  }
   stage_end(p, EER4D_STAGE_DFT_Y, s);
   return e;
 }

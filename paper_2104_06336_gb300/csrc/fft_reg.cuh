@@ -86,15 +86,22 @@ __device__ __forceinline__ float2 twid_dir(const float2* __restrict__ tw, int e,
   return w;
 }
 
-// Column transforms of a [N][ld] complex array, CB columns per CTA,
-// batch = blockIdx.y (in place allowed: every input of the CTA is read before
-// the barrier, every output written after it).
-template <int R1, int R2, int CB, int DIR>
+// Column transforms of a [N][ld] complex array (element n of column c at
+// n*ld_in + c), CB columns per CTA, batch = blockIdx.y.  Output element n of
+// column c goes to n*ld_out + c, or with TOUT (transposed output) to
+// c*ld_out + n, so each column's spectrum is contiguous.  In place is allowed
+// only without TOUT (every input of the CTA is read before the barrier, every
+// output written after it, and CTAs own disjoint columns).
+template <int R1, int R2, int CB, int DIR, bool TOUT>
+__device__ __forceinline__ int colfft_yidx(int k1, int col, int j2) {
+  return TOUT ? ((col * R1 + k1) * (R2 + 1) + 2 * col + j2) : ((k1 * CB + col) * (R2 + 1) + j2);
+}
+
+template <int R1, int R2, int CB, int DIR, bool TOUT>
 __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB)
     k_colfft_reg(const float2* in, float2* out, const float2* __restrict__ tw, int ncols, int ld_in,
                  int ld_out, long long bs_in, long long bs_out, float scale) {
   constexpr int NT = (R1 > R2 ? R1 : R2) * CB;
-  constexpr int PITCH = R2 + 1;
   extern __shared__ float2 sm[];
   const int c0 = blockIdx.x * CB;
   in += blockIdx.y * bs_in;
@@ -109,20 +116,25 @@ __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB)
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const float2 t = (k1 == 0) ? v[k1] : cmul(v[k1], twid_dir(tw, j2 * k1, DIR));
-      sm[(k1 * CB + col) * PITCH + j2] = t;
+      sm[colfft_yidx<R1, R2, CB, DIR, TOUT>(k1, col, j2)] = t;
     }
   }
   __syncthreads();
   for (int g = threadIdx.x; g < R1 * CB; g += NT) {
-    const int col = g % CB, k1 = g / CB, c = c0 + col;
+    int col, k1;
+    if (TOUT) { k1 = g % R1; col = g / R1; } else { col = g % CB; k1 = g / CB; }
+    const int c = c0 + col;
     float2 v[R2];
 #pragma unroll
-    for (int j2 = 0; j2 < R2; ++j2) v[j2] = sm[(k1 * CB + col) * PITCH + j2];
+    for (int j2 = 0; j2 < R2; ++j2) v[j2] = sm[colfft_yidx<R1, R2, CB, DIR, TOUT>(k1, col, j2)];
     dft_reg<R2, DIR>(v);
     if (c < ncols) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2)
-        out[(size_t)(k1 + R1 * k2) * ld_out + c] = make_float2(v[k2].x * scale, v[k2].y * scale);
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int n = k1 + R1 * k2;
+        const size_t o = TOUT ? (size_t)c * ld_out + n : (size_t)n * ld_out + c;
+        out[o] = make_float2(v[k2].x * scale, v[k2].y * scale);
+      }
     }
   }
 }

@@ -76,14 +76,36 @@ __global__ void __launch_bounds__(kThreads) k_validate(const uint32_t* __restric
   if (e1 < e0) e1 = e0;
   unsigned long long sx = 0, sy = 0, sn = 0;
   uint32_t drop = 0;
-  for (uint64_t i = e0 + gtid; i < e1; i += gsz) {
-    const uint32_t v = __ldg(idx + i);
-    if (v >= WH) { ++drop; continue; }
+  auto one = [&](uint32_t v) {
+    if (v >= WH) { ++drop; return; }
     uint32_t y, x;
     dw.divmod(v, y, x);
     sx += x; sy += y; sn += 1;
     if (pacbed) atomicAdd(pacbed + v, 1ull);
+  };
+  // scalar head up to a 16-byte boundary, then 4 x uint4 per thread in flight
+  uint64_t head = e0;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(idx + e0);
+  if ((a & 3) == 0) head = e0 + (((16 - (a & 15)) & 15) >> 2);
+  else head = e1;
+  if (head > e1) head = e1;
+  for (uint64_t i = e0 + gtid; i < head; i += gsz) one(__ldg(idx + i));
+  const uint64_t nv = (e1 - head) >> 2;
+  const uint4* v4 = reinterpret_cast<const uint4*>(idx + head);
+  uint64_t i = gtid;
+  for (; i + 3 * gsz < nv; i += 4 * gsz) {
+    const uint4 q0 = __ldg(v4 + i), q1 = __ldg(v4 + i + gsz), q2 = __ldg(v4 + i + 2 * gsz),
+                q3 = __ldg(v4 + i + 3 * gsz);
+    one(q0.x); one(q0.y); one(q0.z); one(q0.w);
+    one(q1.x); one(q1.y); one(q1.z); one(q1.w);
+    one(q2.x); one(q2.y); one(q2.z); one(q2.w);
+    one(q3.x); one(q3.y); one(q3.z); one(q3.w);
   }
+  for (; i < nv; i += gsz) {
+    const uint4 q = __ldg(v4 + i);
+    one(q.x); one(q.y); one(q.z); one(q.w);
+  }
+  for (uint64_t k = head + 4 * nv + gtid; k < e1; k += gsz) one(__ldg(idx + k));
   if (totals) {
     sx = warp_sum_ll(sx); sy = warp_sum_ll(sy); sn = warp_sum_ll(sn);
     if ((threadIdx.x & 31) == 0 && sn) {
@@ -189,10 +211,12 @@ __global__ void __launch_bounds__(kThreads) k_com(const uint32_t* __restrict__ i
 // ---------------------------------------------------------------- a4 -------
 // Bin + crop + densify.  A CTA owns TF consecutive frames (aligned to
 // multiples of TF in the scan) and all P_pad pixels: it counts into a shared
-// tile of packed 16-bit counters (two frames per word), then writes
-// counts[p][f] as fp16 rows.  No global atomics; every (p, f) of the chunk is
-// written exactly once, zeros included.
-constexpr int kScatStage = 8192;
+// tile of packed 16-bit counters (two frames per word, rows padded by one word
+// so the pixels of a frame fall in different banks), then writes
+// counts[p][f] as fp16, four frames per 8-byte store.  No global atomics;
+// every (p, f) of the chunk is written exactly once, zeros included.  The
+// tile is kept small (<= 48 KB) so several CTAs overlap their phases.
+constexpr int kScatStage = 4096;
 constexpr int kMaxFrameEvents = 65535;
 
 __global__ void __launch_bounds__(kThreads) k_scatter(
@@ -201,50 +225,55 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
     const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int P_pad, int TF,
     uint64_t NR, __half* counts, uint32_t* st) {
   extern __shared__ uint32_t smem[];
-  uint32_t* tile = smem;                                  // [P_pad][TF/2]
-  uint32_t* ev = smem + (size_t)P_pad * (TF / 2);         // [kScatStage]
-  __shared__ unsigned long long s_lo, s_hi;
+  __shared__ uint32_t s_lo[128], s_hi[128];  // event range of each tile frame, relative to E0
+  __shared__ unsigned long long s_e0, s_e1;
   const int TW = TF / 2;
+  const int TP = TW + 1;
+  uint32_t* tile = smem;                     // [P_pad][TP]
+  uint32_t* ev = smem + (size_t)P_pad * TP;  // [kScatStage]
   const uint64_t T0 = (first / TF) * TF;
-  const uint64_t tf0 = T0 + (uint64_t)blockIdx.x * TF;    // global frame of tile column 0
+  const uint64_t tf0 = T0 + (uint64_t)blockIdx.x * TF;  // global frame of tile column 0
   const uint64_t end = first + nfr;
-  for (int i = threadIdx.x; i < P_pad * TW; i += blockDim.x) tile[i] = 0u;
-  if (threadIdx.x == 0) { s_lo = ~0ull; s_hi = 0; }
+  // frames j of the tile inside the chunk: [j0, j1)
+  const int j0 = tf0 < first ? (int)(first - tf0) : 0;
+  const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
+  {
+    uint4* t4 = reinterpret_cast<uint4*>(tile);  // P_pad * TP is a multiple of 4 (P_pad % 16 == 0)
+    const int n4 = P_pad * TP / 4;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (threadIdx.x == 0) { s_e0 = ~0ull; s_e1 = 0; }
   __syncthreads();
-  // frame ranges of the tile's frames that belong to this chunk
   bool bad = false;
-  for (int j = threadIdx.x; j < TF; j += blockDim.x) {
-    const uint64_t g = tf0 + j;
-    if (g < first || g >= end) continue;
-    uint64_t lo, hi;
+  uint64_t lo = 0, hi = 0;
+  if (threadIdx.x >= j0 && threadIdx.x < j1) {
     bool b;
-    frame_range(off, g - first, n_idx, lo, hi, b);
+    frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
     bad |= b;
-    if (hi - lo > kMaxFrameEvents) { bad = true; st_or(st, EER4D_ST_OVERFLOW); }
-    if (hi > lo) { atomicMin(&s_lo, (unsigned long long)lo); atomicMax(&s_hi, (unsigned long long)hi); }
+    if (hi - lo > kMaxFrameEvents) { bad = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
+    if (hi > lo) { atomicMin(&s_e0, (unsigned long long)lo); atomicMax(&s_e1, (unsigned long long)hi); }
   }
   if (bad) st_or(st, EER4D_ST_OFFSETS);
   __syncthreads();
-  const uint64_t E0 = s_lo, E1 = s_hi;
+  const uint64_t E0 = s_e0, E1 = s_e1;
+  if (threadIdx.x < TF) {  // 32-bit event offsets relative to E0 (a tile spans < 2^32 events)
+    const bool in = threadIdx.x >= j0 && threadIdx.x < j1 && hi > lo;
+    s_lo[threadIdx.x] = in ? (uint32_t)(lo - E0) : 0u;
+    s_hi[threadIdx.x] = in ? (uint32_t)(hi - E0) : 0u;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   uint32_t drop = 0;
-  for (uint64_t base = E0; base < E1; base += kScatStage) {
-    const int cnt = (int)min((uint64_t)kScatStage, E1 - base);
+  const uint32_t nev = E1 > E0 ? (uint32_t)(E1 - E0) : 0u;
+  for (uint32_t base = 0; base < nev; base += kScatStage) {
+    const int cnt = (int)min((uint32_t)kScatStage, nev - base);
     __syncthreads();
-    stage_u32(ev, idx + base, cnt);
+    stage_u32(ev, idx + E0 + base, cnt);
     __syncthreads();
-    for (int j = warp; j < TF; j += nw) {
-      const uint64_t g = tf0 + j;
-      if (g < first || g >= end) continue;
-      uint64_t lo, hi;
-      bool b;
-      frame_range(off, g - first, n_idx, lo, hi, b);
-      if (hi - lo > kMaxFrameEvents) hi = lo + kMaxFrameEvents;
-      const uint64_t a = lo > base ? lo : base;
-      const uint64_t e = hi < base + cnt ? hi : base + cnt;
+    for (int j = j0 + warp; j < j1; j += nw) {
+      const uint32_t a = max(s_lo[j], base), e = min(s_hi[j], base + (uint32_t)cnt);
       const uint32_t inc = 1u << (16 * (j & 1));
       uint32_t* col = tile + (j >> 1);
-      for (uint64_t i = a + lane; i < e; i += 32) {
+      for (uint32_t i = a + lane; i < e; i += 32) {
         const uint32_t v = ev[i - base];
         if (v >= WH) { ++drop; continue; }
         uint32_t y, x;
@@ -253,28 +282,34 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
         if ((u | vv) < 0) continue;
         const int p = __ldg(lut2 + vv * pw + u);
         if (p < 0) continue;
-        atomicAdd(col + (size_t)p * TW, inc);
+        atomicAdd(col + p * TP, inc);
       }
     }
   }
   __syncthreads();
-  // write counts[p][tf0 .. tf0+TF) for frames inside the chunk
+  // write counts[p][tf0 + 4w .. tf0 + 4w + 3] (two tile words, four fp16) per lane
   uint32_t over = 0;
-  const bool full = tf0 >= first && tf0 + TF <= end && tf0 + TF <= NR;
-  for (int i = threadIdx.x; i < P_pad * TW; i += blockDim.x) {
-    const int p = i / TW, w = i - p * TW;
-    const uint32_t word = tile[i];
-    const uint32_t c0 = word & 0xffffu, c1 = word >> 16;
-    over += (c0 > 2048u) + (c1 > 2048u);
-    const __half h0 = __ushort2half_rn((unsigned short)c0);
-    const __half h1 = __ushort2half_rn((unsigned short)c1);
-    const uint64_t g = tf0 + 2 * w;
-    __half* dst = counts + (size_t)p * NR + g;
+  const bool full = j0 == 0 && j1 == TF;
+  const int QW = TW / 2;  // 8-byte groups per pixel row
+  for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
+    const int p = i / QW, w = i - p * QW;
+    const uint32_t w0 = tile[p * TP + 2 * w], w1 = tile[p * TP + 2 * w + 1];
+    const uint32_t c0 = w0 & 0xffffu, c1 = w0 >> 16, c2 = w1 & 0xffffu, c3 = w1 >> 16;
+    over += (c0 > 2048u) + (c1 > 2048u) + (c2 > 2048u) + (c3 > 2048u);
+    const __half2 h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
+    const __half2 h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
+    __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
     if (full) {
-      *reinterpret_cast<__half2*>(dst) = __halves2half2(h0, h1);
+      uint2 pk;
+      pk.x = *reinterpret_cast<const uint32_t*>(&h01);
+      pk.y = *reinterpret_cast<const uint32_t*>(&h23);
+      *reinterpret_cast<uint2*>(dst) = pk;
     } else {
-      if (g >= first && g < end && g < NR) dst[0] = h0;
-      if (g + 1 >= first && g + 1 < end && g + 1 < NR) dst[1] = h1;
+      const __half hv[4] = {__low2half(h01), __high2half(h01), __low2half(h23), __high2half(h23)};
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * w + k;
+        if (j >= j0 && j < j1) dst[k] = hv[k];
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -289,18 +324,20 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
 
 }  // namespace
 
+// frames per scatter tile: a multiple of 4 (8-byte count stores), at most
+// 128, with the padded tile P_pad x (TF/2 + 1) words within 48 KB
 int scatter_tf(int P_pad) {
-  int tf = 256;
-  while (tf > 2 && (size_t)P_pad * tf * 2 > 80 * 1024) tf >>= 1;
+  int tf = 128;
+  while (tf > 4 && (size_t)P_pad * (tf / 2 + 1) * 4 > 48 * 1024) tf >>= 1;
   return tf;
 }
 
 cudaError_t launch_validate(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                             const uint64_t* off, uint64_t n_frames, int64_t* pacbed,
                             int64_t* totals, uint32_t* st, cudaStream_t s) {
-  const uint64_t work = n_frames > n_idx ? n_frames : n_idx;
+  const uint64_t work = n_frames > n_idx / 16 ? n_frames : n_idx / 16;
   uint64_t blocks = (work + kThreads - 1) / kThreads;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks == 0) blocks = 1;
   stage_begin(p, EER4D_STAGE_VALIDATE, s);
   k_validate<<<(unsigned)blocks, kThreads, 0, s>>>(
@@ -335,7 +372,7 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
                            uint32_t* st, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int TF = scatter_tf(p->P_pad);
-  const size_t sm = (size_t)p->P_pad * (TF / 2) * 4 + kScatStage * 4;
+  const size_t sm = (size_t)p->P_pad * (TF / 2 + 1) * 4 + kScatStage * 4;
   cudaError_t e = ensure_smem((const void*)k_scatter, sm);
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;

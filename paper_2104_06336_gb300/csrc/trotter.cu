@@ -7,26 +7,29 @@
 //   S(K) = sum_{k in K(K)} G(k, K) exp(-i (chi(k) - chi(k - K')))   [/|K(K)|]
 //   phi  = (N_R / Gbar0) Im(IFFT2(S)),   Gbar0 = mean_{k in BF} G(k, 0).
 // Mask membership is decided in float32 with round-to-nearest products and
-// sums (no fused multiply-add), K'x = c Kx0 - s Ky0, K'y = s Kx0 + c Ky0,
-// Kx0 = m_x kpm_x, so an independent float32 evaluation gives the same set.
+// sums (no fused multiply-add): K'x = c Kx0 - s Ky0, K'y = s Kx0 + c Ky0,
+// Kx0 = m_x kpm_x, d(k, K') = (kx - K'x)^2 + (ky - K'y)^2, so an independent
+// float32 evaluation in the same order gives the same set.
 //
-// G is stored for K_x >= 0 only: G[mx][my][p], G(k, -K) = conj G(k, K).  One
-// warp handles one stored bin b and produces both S(b) (pixels of K(K'(b)),
-// reading G(b)) and S(-b) (pixels of K(K'(-b)), reading conj G(b)), hence
+// G is stored for K_x >= 0 only, with K_y innermost: G[mx][p][my],
+// G(k, -K) = conj G(k, K).  A warp owns 32 consecutive stored bins
+// b = (mx, my0 .. my0+31), one per lane, and walks the bright-field pixels:
+// for each pixel every lane decides membership of its own bin's two sets,
+// K(K'(b)) (reads G(k, b)) and K(K'(-b)) (reads conj G(k, b)); a pixel's
+// G values of the 32 bins are one contiguous 256-byte row, and nearby bins
+// have nearly the same sets, so loads are coalesced and whole sectors are
+// used.  Each lane ends with
 //   H(b) = scale (S(b) - conj S(-b)) / (2 i),
 // the transform of the real image phi: phi = IFFT2(H) with H Hermitian, so
 // the inverse is a real (C2R) transform and V = sum_b |H(b)|^2 / N_R^2
 // (Parseval).  The aberration-weighted spectrum is never written to memory.
-//
-// Per warp and bin: lanes own detector rows and compute, exactly, the integer
-// kx intervals of each disk on their row, then write the member pixels of
-// K(K'(b)) and K(K'(-b)) to two shared lists; lanes then stream the lists
-// (consecutive pixels -> coalesced loads of G) and accumulate.
 #include "common.cuh"
 
 namespace {
 
 constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr int kWarps = EER4D_WARPS_TROTTER;
+constexpr int kBatch = 8;  // pixels per batch of the trotter pixel loop
 
 struct CandCoef {
   float a1, a2, a3, a4;  // chi/(2 pi) = a1 r2 + a2 (qx^2-qy^2) + a3 qx qy + a4 r2^2
@@ -36,7 +39,7 @@ struct CandCoef {
 };
 
 struct TrotParams {
-  int Ny, Nx, nkx, P_pad, n_rows, list_cap;
+  int Ny, Nx, nkx, P_pad, P_bf;
   float kpm_x, kpm_y, k0sq;
   int norm;
   int n_cand;
@@ -89,17 +92,12 @@ __global__ void k_prep(const double* __restrict__ aberr, int n_cand, const short
 }
 
 // Gbar0 = mean over bright-field pixels of G(k, 0); scale = N_R / Gbar0.
-__global__ void k_gbar(const float2* __restrict__ G, const int4* __restrict__ rows, int n_rows,
-                       double NR, double* out) {
+// G(k_p, 0) sits at G[0][p][0] = G[p * Ny].
+__global__ void k_gbar(const float2* __restrict__ G, const int32_t* __restrict__ bfp, int P_bf,
+                       int Ny, double NR, double* out) {
   __shared__ double red[256];
   double s = 0.0;
-  long long n = 0;
-  for (int r = 0; r < n_rows; ++r) {
-    const int4 R = rows[r];
-    const int len = R.z - R.y + 1;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) s += (double)G[R.w + i].x;
-    n += len;
-  }
+  for (int q = threadIdx.x; q < P_bf; q += blockDim.x) s += (double)G[(size_t)bfp[q] * Ny].x;
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -107,49 +105,10 @@ __global__ void k_gbar(const float2* __restrict__ G, const int4* __restrict__ ro
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double g0 = n ? red[0] / (double)n : 0.0;
+    const double g0 = P_bf ? red[0] / (double)P_bf : 0.0;
     out[0] = g0;
     out[1] = g0 != 0.0 ? NR / g0 : 0.0;
   }
-}
-
-// integers x in [L, R] with d(x) = (x - c)^2 + dy2 (float32, rn) < thr
-// (strict) or <= thr; the set is an interval, all of whose points lie in
-// [ceil(c - r) - 1, floor(c + r) + 1], r = sqrt(max(thr - dy2, 0)).
-__device__ __forceinline__ bool disk_pred(int x, float c, float dy2, float thr, bool strict) {
-  const float dx = __fsub_rn((float)x, c);
-  const float d = __fadd_rn(__fmul_rn(dx, dx), dy2);
-  return strict ? (d < thr) : (d <= thr);
-}
-__device__ __forceinline__ void disk_interval(float c, float dy2, float thr, bool strict, int L,
-                                              int R, int& a, int& b) {
-  const float r2 = thr - dy2;
-  const float r = r2 > 0.f ? sqrtf(r2) : 0.f;
-  int a0 = max(L, (int)ceilf(c - r) - 1);
-  int b0 = min(R, (int)floorf(c + r) + 1);
-  while (a0 <= b0 && !disk_pred(a0, c, dy2, thr, strict)) ++a0;
-  while (b0 >= a0 && !disk_pred(b0, c, dy2, thr, strict)) --b0;
-  a = a0;
-  b = b0;
-}
-
-// Member pixels of K(K') on row R (ky, lo, hi, p_lo): up to two segments.
-__device__ __forceinline__ int row_segments(const int4 R, float Kx, float Ky, float k0sq, int& s0a,
-                                            int& s0b, int& s1a, int& s1b) {
-  const float dyi = __fsub_rn((float)R.x, Ky);
-  const float dye = __fsub_rn((float)R.x, -Ky);
-  int a2, b2, a3, b3;
-  disk_interval(Kx, __fmul_rn(dyi, dyi), k0sq, true, R.y, R.z, a2, b2);
-  s0a = 1; s0b = 0; s1a = 1; s1b = 0;
-  if (a2 > b2) return 0;
-  disk_interval(-Kx, __fmul_rn(dye, dye), k0sq, false, R.y, R.z, a3, b3);
-  if (a3 > b3 || b3 < a2 || a3 > b2) {
-    s0a = a2; s0b = b2;
-  } else {
-    s0a = a2; s0b = min(b2, a3 - 1);
-    s1a = max(a2, b3 + 1); s1b = b2;
-  }
-  return max(0, s0b - s0a + 1) + max(0, s1b - s1a + 1);
 }
 
 __device__ __forceinline__ void kprime(const CandCoef& c0, float kpm_x, float kpm_y, int m_x,
@@ -160,77 +119,15 @@ __device__ __forceinline__ void kprime(const CandCoef& c0, float kpm_x, float kp
   Ky = __fadd_rn(__fmul_rn(c0.s, kx0), __fmul_rn(c0.c, ky0));
 }
 
-// Builds list[0..n) of member pixels of K(K') for the warp (all lanes call).
-__device__ __forceinline__ int build_list(const int4* __restrict__ srows, int n_rows, float Kx,
-                                          float Ky, float k0sq, uint16_t* list) {
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  for (int r0 = 0; r0 < n_rows; r0 += 32) {
-    const int r = r0 + lane;
-    int s0a = 1, s0b = 0, s1a = 1, s1b = 0, cnt = 0;
-    int4 R = make_int4(0, 0, -1, 0);
-    if (r < n_rows) {
-      R = srows[r];
-      cnt = row_segments(R, Kx, Ky, k0sq, s0a, s0b, s1a, s1b);
-    }
-    int total;
-    int pos = base + warp_excl_scan(cnt, total);
-    for (int x = s0a; x <= s0b; ++x) list[pos++] = (uint16_t)(R.w + (x - R.y));
-    for (int x = s1a; x <= s1b; ++x) list[pos++] = (uint16_t)(R.w + (x - R.y));
-    base += total;
-  }
-  __syncwarp();
-  return base;
+// |k - K|^2 in float32, round-to-nearest, products then sum (the mask rule)
+__device__ __forceinline__ float dist2(float kx, float ky, float Kx, float Ky) {
+  const float dx = __fsub_rn(kx, Kx), dy = __fsub_rn(ky, Ky);
+  return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
 }
 
-template <bool GRAD>
-struct Acc {
-  float2 S;
-  float2 D[GRAD ? 5 : 1];
-};
-
-// Streams one list: term = g * exp(-i chi(k)) exp(+i chi(q)), q = k - K'.
-template <bool GRAD, bool CONJ>
-__device__ __forceinline__ void accumulate(const uint16_t* list, int n, const float2* __restrict__ Gb,
-                                           const short2* __restrict__ spix,
-                                           const float2* __restrict__ ekc, const CandCoef& cf,
-                                           float Kx, float Ky, Acc<GRAD>& acc) {
-  const int lane = threadIdx.x & 31;
-  for (int j = lane; j < n; j += 32) {
-    const int p = list[j];
-    float2 g = __ldg(Gb + p);
-    if (CONJ) g.y = -g.y;
-    const short2 kk = spix[p];
-    const float kx = (float)kk.x, ky = (float)kk.y;
-    const float qx = kx - Kx, qy = ky - Ky;
-    const float t = chi_turns(cf, qx, qy);
-    float sn, cs;
-    sincospif(2.f * t, &sn, &cs);
-    const float2 e = __ldg(ekc + p);
-    const float2 ph = make_float2(e.x * cs - e.y * sn, e.x * sn + e.y * cs);
-    const float2 term = cmul(g, ph);
-    acc.S = cadd(acc.S, term);
-    if constexpr (GRAD) {
-      const float r2k = fmaf(kx, kx, ky * ky), r2q = fmaf(qx, qx, qy * qy);
-      const float d1 = cf.u1 * (r2k - r2q);
-      const float d2 = cf.u1 * ((kx - ky) * (kx + ky) - (qx - qy) * (qx + qy));
-      const float d3 = cf.u3 * (kx * ky - qx * qy);
-      const float d4 = cf.u4 * (r2k * r2k - r2q * r2q);
-      const float s4 = 4.f * cf.a4 * r2q;
-      const float gx = fmaf(2.f * (cf.a1 + cf.a2) + s4, qx, cf.a3 * qy);
-      const float gy = fmaf(2.f * (cf.a1 - cf.a2) + s4, qy, cf.a3 * qx);
-      const float d5 = kTwoPi * (gy * Kx - gx * Ky);
-      const float2 mi = make_float2(term.y, -term.x);  // -i * term
-      acc.D[0] = make_float2(fmaf(d1, mi.x, acc.D[0].x), fmaf(d1, mi.y, acc.D[0].y));
-      acc.D[1] = make_float2(fmaf(d2, mi.x, acc.D[1].x), fmaf(d2, mi.y, acc.D[1].y));
-      acc.D[2] = make_float2(fmaf(d3, mi.x, acc.D[2].x), fmaf(d3, mi.y, acc.D[2].y));
-      acc.D[3] = make_float2(fmaf(d4, mi.x, acc.D[3].x), fmaf(d4, mi.y, acc.D[3].y));
-      acc.D[4] = make_float2(fmaf(d5, mi.x, acc.D[4].x), fmaf(d5, mi.y, acc.D[4].y));
-    }
-  }
+__device__ __forceinline__ float2 cmadd(float2 acc, float2 a, float w) {
+  return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
 }
-
-__device__ __forceinline__ float2 warp_csum(float2 v) { return make_float2(warp_sum(v.x), warp_sum(v.y)); }
 
 // H = scale (A/na - conj(B/nb)) / (2i), with A/n = 0 when n = 0 under area norm.
 __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, int norm, float scale) {
@@ -242,100 +139,209 @@ __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, in
   return make_float2(0.5f * scale * X.y, -0.5f * scale * X.x);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(EER4D_WARPS_TROTTER * 32)
-    k_trotter(TrotParams P, const float2* __restrict__ G, const short2* __restrict__ pix,
-              const int4* __restrict__ rows, const CandCoef* __restrict__ coef,
+// MODE: TROT_FWD (H for NC candidates per pass), TROT_GRAD (adjoint against
+// W = FFT(upstream gradient)), TROT_VARGRAD (V and dV/dtheta), TROT_COUNT
+// (|K(K)| per bin).
+template <int MODE, int NC>
+__global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 3)
+    k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
+              const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
               const float2* __restrict__ W, float2* H, double* partial, int32_t* count) {
-  extern __shared__ unsigned char smem_raw[];
-  short2* spix = reinterpret_cast<short2*>(smem_raw);
-  int4* srows = reinterpret_cast<int4*>(spix + P.P_pad);
-  uint16_t* lists = reinterpret_cast<uint16_t*>(srows + P.n_rows);
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
-  constexpr int NV = GRAD ? 5 : 1;
-  __shared__ double sred[EER4D_WARPS_TROTTER][5];
+  extern __shared__ unsigned char smem_raw[];
+  float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
+  int* sp = reinterpret_cast<int*>(skk + P.P_bf);                      // [P_bf] kept-pixel index
+  float2* sek = reinterpret_cast<float2*>(sp + ((P.P_bf + 1) & ~1));  // [NC][P_bf]
+  __shared__ double sred[GRAD ? kWarps * 32 : 1][5];
 
-  for (int i = threadIdx.x; i < P.P_pad; i += blockDim.x) spix[i] = pix[i];
-  for (int i = threadIdx.x; i < P.n_rows; i += blockDim.x) srows[i] = rows[i];
-  __syncthreads();
-
+  for (int q = threadIdx.x; q < P.P_bf; q += blockDim.x) {
+    const int p = bfp[q];
+    const short2 k = pix[p];
+    skk[q] = make_float2((float)k.x, (float)k.y);
+    sp[q] = p;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* listP = lists + (size_t)warp * 2 * P.list_cap;
-  uint16_t* listM = listP + P.list_cap;
   const CandCoef c0 = coef[0];
-  const float scale = (float)gscale[1];
-  const int ntask = P.nkx * P.Ny;
-  const int gw = blockIdx.x * EER4D_WARPS_TROTTER + warp;
-  const int nwarps = gridDim.x * EER4D_WARPS_TROTTER;
-  double gacc[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) gacc[j] = 0.0;
+  const float scale = MODE == TROT_COUNT ? 0.f : (float)gscale[1];
+  const int nyw = (P.Ny + 31) >> 5;
+  const int ntask = P.nkx * nyw;
+  const int gw = blockIdx.x * kWarps + warp;
+  const int nwarps = gridDim.x * kWarps;
+  double gacc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int npass = (MODE == TROT_FWD) ? (P.n_cand + NC - 1) / NC : 1;
 
-  for (int t = gw; t < ntask; t += nwarps) {
-    const int mx = t / P.Ny, my = t - mx * P.Ny;
-    const int mmx = (P.Nx - mx) % P.Nx, mmy = (P.Ny - my) % P.Ny;
-    float Kpx, Kpy, Kmx, Kmy;
-    kprime(c0, P.kpm_x, P.kpm_y, freq_index(mx, P.Nx), freq_index(my, P.Ny), Kpx, Kpy);
-    kprime(c0, P.kpm_x, P.kpm_y, freq_index(mmx, P.Nx), freq_index(mmy, P.Ny), Kmx, Kmy);
-    const int nP = build_list(srows, P.n_rows, Kpx, Kpy, P.k0sq, listP);
-    const int nM = build_list(srows, P.n_rows, Kmx, Kmy, P.k0sq, listM);
-    if (MODE == TROT_COUNT) {
-      if (lane == 0) {
+  for (int pass = 0; pass < npass; ++pass) {
+    const int cb = pass * NC;
+    const int ncp = (MODE == TROT_FWD) ? min(NC, P.n_cand - cb) : 1;
+    __syncthreads();
+    if (MODE != TROT_COUNT) {
+      for (int i = threadIdx.x; i < ncp * P.P_bf; i += blockDim.x) {
+        const int c = i / P.P_bf, q = i - c * P.P_bf;
+        sek[c * P.P_bf + q] = ek[(size_t)(cb + c) * P.P_pad + sp[q]];
+      }
+    }
+    __syncthreads();
+    CandCoef cf[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cf[c] = coef[cb + (c < ncp ? c : 0)];
+
+    for (int t = gw; t < ntask; t += nwarps) {
+      const int mx = t / nyw;
+      const int my = (t - mx * nyw) * 32 + lane;
+      const bool active = my < P.Ny;
+      const int mys = active ? my : 0;
+      const int mmx = (P.Nx - mx) % P.Nx, mmy = (P.Ny - mys) % P.Ny;
+      float Kpx, Kpy, Kmx, Kmy;
+      kprime(c0, P.kpm_x, P.kpm_y, freq_index(mx, P.Nx), freq_index(mys, P.Ny), Kpx, Kpy);
+      kprime(c0, P.kpm_x, P.kpm_y, freq_index(mmx, P.Nx), freq_index(mmy, P.Ny), Kmx, Kmy);
+      // off Nyquist K'(-b) = -K'(b) exactly and both sets use the same two distances
+      const bool nyq = (2 * mx == P.Nx) || (2 * mys == P.Ny);
+      const float2* Gl = G + (size_t)mx * P.P_pad * P.Ny + mys;
+      float2 SP[NC], SM[NC];
+      float2 DP[GRAD ? 5 : 1], DM[GRAD ? 5 : 1];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) SP[c] = SM[c] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < (GRAD ? 5 : 1); ++j) DP[j] = DM[j] = make_float2(0.f, 0.f);
+      int nP = 0, nM = 0;
+      // the warp's bins include a Nyquist bin (uniform across the warp, no intrinsic)
+      const int my0 = (t - mx * nyw) * 32;
+      const bool nyq_warp = (2 * mx == P.Nx) || (P.Ny / 2 >= my0 && P.Ny / 2 < my0 + 32);
+      // one pair (k_q, b) of one set: term = g exp(-i chi(k)) exp(+i chi(k - K)),
+      // added to S(b) with weight wp and to S(-b) with weight 1 - wp
+      auto contrib = [&](float2 g, float Kx, float Ky, float2 kk, int q, float wp,
+                         float2 (&SPa)[NC], float2 (&SMa)[NC], float2 (&DPa)[GRAD ? 5 : 1],
+                         float2 (&DMa)[GRAD ? 5 : 1]) {
+        const float qx = kk.x - Kx, qy = kk.y - Ky;
+        const float wm = 1.f - wp;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (c >= ncp) break;
+          const float tq = chi_turns(cf[c], qx, qy);
+          const float fr = tq - rintf(tq);  // exact: phase in turns reduced to [-1/2, 1/2]
+          float sn, cs;
+          __sincosf(kTwoPi * fr, &sn, &cs);
+          const float2 e = sek[c * P.P_bf + q];
+          const float2 ph = make_float2(e.x * cs - e.y * sn, e.x * sn + e.y * cs);
+          const float2 term = cmul(g, ph);
+          SPa[c] = cmadd(SPa[c], term, wp);
+          SMa[c] = cmadd(SMa[c], term, wm);
+          if constexpr (GRAD) {
+            const CandCoef& f = cf[0];
+            const float kx = kk.x, ky = kk.y;
+            const float r2k = fmaf(kx, kx, ky * ky), r2q = fmaf(qx, qx, qy * qy);
+            float d[5];
+            d[0] = f.u1 * (r2k - r2q);
+            d[1] = f.u1 * ((kx - ky) * (kx + ky) - (qx - qy) * (qx + qy));
+            d[2] = f.u3 * (kx * ky - qx * qy);
+            d[3] = f.u4 * (r2k * r2k - r2q * r2q);
+            const float s4 = 4.f * f.a4 * r2q;
+            const float gx = fmaf(2.f * (f.a1 + f.a2) + s4, qx, f.a3 * qy);
+            const float gy = fmaf(2.f * (f.a1 - f.a2) + s4, qy, f.a3 * qx);
+            d[4] = kTwoPi * (gy * Kx - gx * Ky);
+            const float2 mi = make_float2(term.y, -term.x);  // -i * term
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+              DPa[j] = cmadd(DPa[j], mi, d[j] * wp);
+              DMa[j] = cmadd(DMa[j], mi, d[j] * wm);
+            }
+          }
+        }
+      };
+
+      // Pixels in batches of kBatch: memberships first, then every member's G
+      // load issued before any is used (kBatch loads in flight per lane).
+      for (int q0 = 0; q0 < P.P_bf; q0 += kBatch) {
+        unsigned mP = 0u, mM = 0u;
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+          const int q = q0 + i;
+          if (q >= P.P_bf) break;
+          const float2 kk = skk[q];
+          const float dm = dist2(kk.x, kk.y, Kpx, Kpy);
+          const float dp = dist2(kk.x, kk.y, -Kpx, -Kpy);
+          const bool memP = active && dm < P.k0sq && dp > P.k0sq;
+          bool memM;
+          if (!nyq) {
+            memM = active && dp < P.k0sq && dm > P.k0sq;
+          } else {
+            const float em = dist2(kk.x, kk.y, Kmx, Kmy);
+            const float ep = dist2(kk.x, kk.y, -Kmx, -Kmy);
+            memM = active && em < P.k0sq && ep > P.k0sq;
+          }
+          mP |= (unsigned)memP << i;
+          mM |= (unsigned)memM << i;
+        }
+        nP += __popc(mP);
+        nM += __popc(mM);
+        if (MODE == TROT_COUNT) continue;
+        const unsigned mAny = mP | mM;
+        if (mAny == 0u) continue;
+        float2 gb[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i)
+          gb[i] = ((mAny >> i) & 1u) ? Gl[(size_t)sp[q0 + i] * P.Ny] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+          const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
+          if (!(memP || memM)) continue;
+          const int q = q0 + i;
+          const float2 kk = skk[q];
+          const float2 g = gb[i];
+          // Off Nyquist the two sets are disjoint, so one term per pixel: G into
+          // S(b) or conj(G) into S(-b).  At a Nyquist bin K'(-b) equals K'(b) in
+          // that component and a pixel may be in both sets: two terms.
+          if (!nyq_warp) {
+            const float2 gg = memM ? make_float2(g.x, -g.y) : g;
+            contrib(gg, memM ? Kmx : Kpx, memM ? Kmy : Kpy, kk, q, memM ? 0.f : 1.f, SP, SM, DP, DM);
+          } else {
+            if (memP) contrib(g, Kpx, Kpy, kk, q, 1.f, SP, SM, DP, DM);
+            if (memM) contrib(make_float2(g.x, -g.y), Kmx, Kmy, kk, q, 0.f, SP, SM, DP, DM);
+          }
+        }
+      }
+
+      if (!active) continue;
+      if (MODE == TROT_COUNT) {
         count[my * P.Nx + mx] = nP;
         count[mmy * P.Nx + mmx] = nM;
+        continue;
       }
-      __syncwarp();
-      continue;
-    }
-    const float2* Gb = G + (size_t)t * P.P_pad;
-    const float wgt = (mx == 0 || 2 * mx == P.Nx) ? 1.f : 2.f;
-    const int nc = (MODE == TROT_FWD) ? P.n_cand : 1;
-    for (int c = 0; c < nc; ++c) {
-      const CandCoef cf = (c == 0) ? c0 : coef[c];
-      const float2* ekc = ek + (size_t)c * P.P_pad;
-      Acc<GRAD> ap, am;
-      ap.S = am.S = make_float2(0.f, 0.f);
+      const float wgt = (mx == 0 || 2 * mx == P.Nx) ? 1.f : 2.f;
 #pragma unroll
-      for (int j = 0; j < (GRAD ? 5 : 1); ++j) ap.D[j] = am.D[j] = make_float2(0.f, 0.f);
-      accumulate<GRAD, false>(listP, nP, Gb, spix, ekc, cf, Kpx, Kpy, ap);
-      accumulate<GRAD, true>(listM, nM, Gb, spix, ekc, cf, Kmx, Kmy, am);
-      ap.S = warp_csum(ap.S);
-      am.S = warp_csum(am.S);
-      const float2 Hb = combine(ap.S, am.S, nP, nM, P.norm, scale);
-      if (MODE != TROT_GRAD && lane == 0) H[((size_t)c * P.Ny + my) * P.nkx + mx] = Hb;
-      if constexpr (GRAD) {
-        float2 wb;
-        double f;
-        if (MODE == TROT_VARGRAD) {  // dV/dtheta: w = 2 H / N_R, factor 1/N_R
-          wb = Hb;
-          f = 2.0 / ((double)P.NR * (double)P.NR);
-        } else {
-          wb = __ldg(W + (size_t)my * P.nkx + mx);
-          f = 1.0 / (double)P.NR;
-        }
+      for (int c = 0; c < NC; ++c) {
+        if (c >= ncp) break;
+        const float2 Hb = combine(SP[c], SM[c], nP, nM, P.norm, scale);
+        if (MODE != TROT_GRAD) H[((size_t)(cb + c) * P.Ny + my) * P.nkx + mx] = Hb;
+        if constexpr (GRAD) {
+          float2 wb;
+          double f;
+          if (MODE == TROT_VARGRAD) {  // dV/dtheta: w = 2 H / N_R, factor 1/N_R
+            wb = Hb;
+            f = 2.0 / ((double)P.NR * (double)P.NR);
+          } else {
+            wb = __ldg(W + (size_t)my * P.nkx + mx);
+            f = 1.0 / (double)P.NR;
+          }
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          const float2 dp = warp_csum(ap.D[j]);
-          const float2 dm = warp_csum(am.D[j]);
-          const float2 dH = combine(dp, dm, nP, nM, P.norm, scale);
-          // Re(dH * conj(w))
-          const double re = (double)dH.x * (double)wb.x + (double)dH.y * (double)wb.y;
-          gacc[j] += (double)wgt * f * re;
+          for (int j = 0; j < 5; ++j) {
+            const float2 dH = combine(DP[j], DM[j], nP, nM, P.norm, scale);
+            gacc[j] += (double)wgt * f * ((double)dH.x * (double)wb.x + (double)dH.y * (double)wb.y);
+          }
         }
       }
     }
   }
   if constexpr (GRAD) {
-    if (lane == 0) {
+    // fixed-order block sum of the per-thread partials (no warp intrinsics)
 #pragma unroll
-      for (int j = 0; j < NV; ++j) sred[warp][j] = gacc[j];
-    }
+    for (int j = 0; j < 5; ++j) sred[threadIdx.x][j] = gacc[j];
     __syncthreads();
-    if (threadIdx.x < NV) {
+    if (threadIdx.x < 5) {
       double s = 0.0;
-      for (int w = 0; w < EER4D_WARPS_TROTTER; ++w) s += sred[w][threadIdx.x];
-      partial[(size_t)blockIdx.x * NV + threadIdx.x] = s;
+      for (int i = 0; i < kWarps * 32; ++i) s += sred[i][threadIdx.x];
+      partial[(size_t)blockIdx.x * 5 + threadIdx.x] = s;
     }
   }
 }
@@ -404,10 +410,23 @@ __global__ void k_ascent(double* theta, const double* step, const double* grad) 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int trot_blocks(const eer4d_plan* p) {
-  const int ntask = p->nkx * (int)p->g.scan_ny;
-  int b = (ntask + EER4D_WARPS_TROTTER - 1) / EER4D_WARPS_TROTTER;
-  return b < 152 * 8 ? b : 152 * 8;
+constexpr int kNcFwd = 4;  // candidates per pass of the forward kernel
+
+constexpr int kMaxTrotBlocks = 2048;  // capacity of the per-block partial sums
+
+// One full wave of the persistent grid: SMs x resident blocks per SM (from the
+// occupancy calculator), never more blocks than warp tasks need.
+int trot_blocks(const eer4d_plan* p, const void* kern, size_t smem) {
+  const int ntask = p->nkx * (((int)p->g.scan_ny + 31) / 32);
+  const int need = (ntask + kWarps - 1) / kWarps;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
+  int b = nsm * (occ > 0 ? occ : 1);
+  if (b > need) b = need;
+  if (b > kMaxTrotBlocks) b = kMaxTrotBlocks;
+  return b < 1 ? 1 : b;
 }
 
 struct Layout {
@@ -421,10 +440,25 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   L.gscale = o; o = align256(o + 2 * sizeof(double));
   const int nh = (mode == TROT_GRAD || mode == TROT_COUNT) ? 0 : n_cand;
   L.H = o; o = align256(o + sizeof(float2) * (size_t)nh * p->g.scan_ny * p->nkx);
-  L.partial = o; o = align256(o + sizeof(double) * 5 * trot_blocks(p));
+  L.partial = o; o = align256(o + sizeof(double) * 5 * kMaxTrotBlocks);
   L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)nh);
   L.total = o;
   return L;
+}
+
+template <int MODE, int NC>
+cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
+                     const CandCoef* coef, const float2* ek, const double* gsc, const float2* W,
+                     float2* H, double* partial, int32_t* count, int* nblk, cudaStream_t s) {
+  const size_t sm = sizeof(float2) * p->P_bf + sizeof(int) * ((p->P_bf + 1) & ~1) +
+                    sizeof(float2) * (size_t)NC * p->P_bf;
+  const void* kern = (const void*)k_trotter<MODE, NC>;
+  cudaError_t e = ensure_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  *nblk = trot_blocks(p, kern, sm);
+  k_trotter<MODE, NC><<<*nblk, kWarps * 32, sm, s>>>(tp, G, p->d_bfp, p->d_pix, coef, ek, gsc, W,
+                                                     H, partial, count);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -455,36 +489,38 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   stage_begin(p, EER4D_STAGE_TROTTER, s);
   k_prep<<<n_cand, 256, 0, s>>>(aberr, n_cand, p->d_pix, p->P_pad, p->P, p->g.dalpha_rad,
                                 p->g.lambda_A, coef, ek, st);
+  count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mode != TROT_COUNT) {
-    k_gbar<<<1, 256, 0, s>>>(G, p->d_rows, p->n_rows, (double)p->F, gsc);
+    k_gbar<<<1, 256, 0, s>>>(G, p->d_bfp, p->P_bf, (int)p->g.scan_ny, (double)p->F, gsc);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   TrotParams tp;
   tp.Ny = p->g.scan_ny; tp.Nx = p->g.scan_nx; tp.nkx = p->nkx; tp.P_pad = p->P_pad;
-  tp.n_rows = p->n_rows; tp.list_cap = p->list_max;
+  tp.P_bf = p->P_bf;
   tp.kpm_x = (float)p->g.kpm_x; tp.kpm_y = (float)p->g.kpm_y;
   tp.k0sq = (float)(p->g.k0_px * p->g.k0_px);
   tp.norm = p->norm; tp.n_cand = n_cand; tp.NR = (float)p->F;
-  const size_t sm = sizeof(short2) * p->P_pad + sizeof(int4) * p->n_rows +
-                    sizeof(uint16_t) * 2 * (size_t)p->list_max * EER4D_WARPS_TROTTER;
-  const int nblk = trot_blocks(p);
-  const dim3 blk(EER4D_WARPS_TROTTER * 32);
-#define EER4D_LAUNCH_TROT(M)                                                                       \
-  do {                                                                                            \
-    if ((e = ensure_smem((const void*)k_trotter<M>, sm)) != cudaSuccess) return e;               \
-    k_trotter<M><<<nblk, blk, sm, s>>>(tp, G, p->d_pix, p->d_rows, coef, ek, gsc, W, H, partial, \
-                                       count_out);                                                \
-  } while (0)
+  int nblk = 1;
   switch (mode) {
-    case TROT_FWD: EER4D_LAUNCH_TROT(TROT_FWD); break;
-    case TROT_GRAD: EER4D_LAUNCH_TROT(TROT_GRAD); break;
-    case TROT_VARGRAD: EER4D_LAUNCH_TROT(TROT_VARGRAD); break;
-    default: EER4D_LAUNCH_TROT(TROT_COUNT); break;
+    case TROT_FWD:
+      e = n_cand == 1
+              ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s)
+              : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      break;
+    case TROT_GRAD:
+      e = launch_k<TROT_GRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      break;
+    case TROT_VARGRAD:
+      e = launch_k<TROT_VARGRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      break;
+    default:
+      e = launch_k<TROT_COUNT, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      break;
   }
-#undef EER4D_LAUNCH_TROT
-  count_launches(mode == TROT_COUNT ? 2 : 3);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launches(1);
+  if (e != cudaSuccess) return e;
   if (mode == TROT_GRAD || mode == TROT_VARGRAD) {
     k_reduce_partials<<<1, 256, 0, s>>>(partial, nblk, 5, grad_out);
     count_launches(1);

@@ -21,9 +21,10 @@ def as_u32(idx: torch.Tensor) -> torch.Tensor:
 class Reconstructor:
     """Plan + workspace for one scan geometry on one GPU.
 
-    ``geom`` uses the field names of eer4d_geom.  Buffers:
-    counts fp16 [P_pad][F], G complex64 [nkx][Ny][P_pad], scratch bytes,
-    status int32[4] (zeroed at construction; see ``check``)."""
+    ``geom`` uses the field names of eer4d_geom.  Buffers: ``work`` (the
+    accumulation workspace of ssb_accumulate; ``counts`` is its fp16
+    [P_pad][F] head), G complex64 [nkx][P_pad][Ny], scratch bytes, status
+    int32[4] (zeroed at construction; see ``check``)."""
 
     def __init__(self, geom: dict, precision: int = L.FP32_FFT, norm: int = L.NORM_NONE,
                  n_cand: int = 1, device=None, alloc_counts: bool = True):
@@ -34,7 +35,10 @@ class Reconstructor:
             self.plan = L.Plan(geom, precision, norm)
             cb, gb, sb = self.plan.workspace_bytes(n_cand)
             self.n_cand = n_cand
-            self.counts = torch.empty(cb // 2, dtype=torch.float16, device=self.device) if alloc_counts else None
+            self.work = torch.empty(cb, dtype=torch.uint8, device=self.device) if alloc_counts else None
+            info = self.plan.info
+            n_counts = info["P_pad"] * geom["scan_ny"] * geom["scan_nx"]
+            self.counts = self.work[:2 * n_counts].view(torch.float16) if alloc_counts else None
             self.G = torch.empty(gb // 4, dtype=torch.float32, device=self.device)
             self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
             self.status = torch.zeros(4, dtype=torch.int32, device=self.device)
@@ -60,7 +64,7 @@ class Reconstructor:
         step = F if chunk_frames is None else int(chunk_frames)
         for f0 in range(0, F, step):
             f1 = min(F, f0 + step)
-            L.ssb_accumulate(self.plan, idx, off[f0:f1 + 1], f0, self.counts, self.G, f1 == F,
+            L.ssb_accumulate(self.plan, idx, off[f0:f1 + 1], f0, self.work, self.G, f1 == F,
                              status=self.status)
 
     def com_dpc(self, idx: torch.Tensor, off: torch.Tensor, lam1=0.0, lam2=0.0, use_totals=True,
@@ -110,9 +114,9 @@ class Reconstructor:
 
     # -- views -----------------------------------------------------------------
     def G_complex(self) -> torch.Tensor:
-        """G as complex64 [nkx][Ny][P_pad] (K_x >= 0 half)."""
+        """G as complex64 [nkx][P_pad][Ny] (K_x >= 0 half, K_y innermost)."""
         nkx, P_pad = self.info["nkx"], self.info["P_pad"]
-        return torch.view_as_complex(self.G.view(nkx, self.Ny, P_pad, 2))
+        return torch.view_as_complex(self.G.view(nkx, P_pad, self.Ny, 2))
 
     def check(self, raise_on_error: bool = True) -> int:
         code = L.status_code(self.status)

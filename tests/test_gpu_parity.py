@@ -60,12 +60,12 @@ class Case:
 
     def G_gpu_full(self):
         """GPU half spectrum expanded to [P][Ny][Nx] with G(-K) = conj G(K)."""
-        Gh = self.rec.G_complex().cpu().numpy().astype(np.complex128)  # [nkx][Ny][P_pad]
+        Gh = self.rec.G_complex().cpu().numpy().astype(np.complex128)  # [nkx][P_pad][Ny]
         P = self.rec.info["P"]
         Ny, Nx = self.w.scan_ny, self.w.scan_nx
         out = np.zeros((P, Ny, Nx), dtype=np.complex128)
         nkx = Nx // 2 + 1
-        out[:, :, :nkx] = np.transpose(Gh[:, :, :P], (2, 1, 0))
+        out[:, :, :nkx] = np.transpose(Gh[:, :P, :], (1, 2, 0))
         for mx in range(nkx, Nx):
             src = out[:, :, Nx - mx]
             out[:, :, mx] = np.conj(src[:, (-np.arange(Ny)) % Ny])
@@ -292,7 +292,7 @@ def test_pixel_overflow_flagged():
 def test_out_of_order_chunks_rejected(c1):
     import paper_2104_06336_gb300 as P
     with pytest.raises(P.Eer4dError) as e:
-        P.ssb_accumulate(c1.rec.plan, c1.idx, c1.off[64:129], 64, c1.rec.counts, c1.rec.G, False)
+        P.ssb_accumulate(c1.rec.plan, c1.idx, c1.off[64:129], 64, c1.rec.work, c1.rec.G, False)
     assert e.value.code == P._lib.EER4D_EORDER
 
 
