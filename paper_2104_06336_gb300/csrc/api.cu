@@ -90,6 +90,8 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_rows);
   cudaFree(p->d_tw_y);
   cudaFree(p->d_tw_x);
+  cudaFree(p->d_dft_hi);
+  cudaFree(p->d_dft_lo);
   free(p);
 }
 
@@ -220,6 +222,11 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
     free_plan(p);
     return rc;
   }
+  if (precision == EER4D_SPLIT_FP16 && (e = make_dftx_tc(p)) != cudaSuccess) {
+    const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
+    free_plan(p);
+    return rc;
+  }
   p->next_frame = 0;
   *out = p;
   return EER4D_OK;
@@ -325,7 +332,10 @@ int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
                                     d_status, s));
   if (rc != EER4D_OK) return rc;
   const uint64_t Nx = p->g.scan_nx;
-  rc = cuda_fail(launch_stage1(p, counts, X1, (int)(first_frame / Nx), (int)(end / Nx), s));
+  const int ya = (int)(first_frame / Nx), yb = (int)(end / Nx);
+  rc = cuda_fail(p->precision == EER4D_SPLIT_FP16
+                     ? launch_stage1_tc(p, counts, X1, ya, yb, d_status, s)
+                     : launch_stage1(p, counts, X1, ya, yb, s));
   if (rc != EER4D_OK) return rc;
   p->next_frame = end;
   if (is_last) {

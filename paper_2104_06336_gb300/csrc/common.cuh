@@ -62,6 +62,8 @@ struct eer4d_plan {
   int32_t* d_lut2;           // [ph*pw] kept pixel index or -1
   short2* d_pix;             // [P_pad] (kx, ky)
   int32_t* d_bfp;            // [P_bf] kept-pixel index of each bright-field pixel (row-major)
+  __half* d_dft_hi;          // split-FP16 DFT matrix along x (tile-blocked), SPLIT_FP16 plans
+  __half* d_dft_lo;
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
   float2* d_tw_y;            // [scan_ny]
   float2* d_tw_x;            // [scan_nx]
@@ -131,6 +133,9 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
 cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
                           cudaStream_t s);
 cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cudaStream_t s);
+cudaError_t make_dftx_tc(eer4d_plan* p);
+cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
+                             uint32_t* st, cudaStream_t s);
 cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, int batch,
                              cudaStream_t s);
 // accumulation workspace of ssb_accumulate: fp16 counts [P_pad][F], then (at a

@@ -1,0 +1,309 @@
+// Split-FP16 tensor-core DFT along the scan x axis (the G function of Sec. IV,
+// first of its two 1D transforms) on the 5th-generation tensor cores.
+//
+// X1[p, y][k] = sum_x counts[p, y][x] exp(-2 pi i k x / Nx), k = 0 .. Nx/2,
+// is a real GEMM D = A B^T with A[m][x] = counts (pixel rows at one scan row
+// y; integers <= 2048, exact in fp16) and B[n][x] = (cos, -sin)(2 pi k x/Nx)
+// for n = 2k, 2k+1.  B = B_hi + B_lo with B_hi = fp16(B), B_lo = fp16(B - B_hi)
+// (about 22 significant bits together); both products accumulate in one FP32
+// accumulator in tensor memory: D = A B_hi^T + A B_lo^T.
+//
+// Per CTA: 128 pixel rows (M) at one y; N tiles of 256 columns; K tiles of 64.
+// Operands are staged in shared memory in the no-swizzle K-major core-matrix
+// layout (8 rows x 16 bytes per core matrix; leading-dimension offset 128 B
+// between K-adjacent core matrices, stride offset 1024 B between 8-row
+// groups).  One thread issues tcgen05.mma (kind::f16, M = 128, N = 256,
+// K = 16) and commits to an mbarrier; every wait on it is bounded by a
+// %globaltimer limit and, on expiry, sets EER4D_ST_TIMEOUT, stops issuing and
+// still frees the tensor memory.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kM = 128;       // rows per CTA (pixels)
+constexpr int kN = 256;       // accumulator columns per N tile
+constexpr int kK = 64;        // K per stage (fp16: 128 bytes per row)
+constexpr int kThreadsTC = 256;
+constexpr int kTileA = kM * kK * 2;   // 16 KB
+constexpr int kTileB = kN * kK * 2;   // 32 KB
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;  // 200 ms
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (r, k) in a K-major no-swizzle tile with kK columns
+__device__ __forceinline__ uint32_t cm_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30),
+// SBO >> 4 [32,46), descriptor version 1 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D f32 (bit 4), A/B f16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: returns false if the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 16 consecutive 32-bit accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// counts: fp16 [P_pad][Ny*Nx]; Bhi/Blo: tile-blocked [NT][KT][kN x kK] in the
+// shared core-matrix layout; X1: complex64 [nkx][Ny][P_pad].  grid = (pixel
+// tiles of 128, scan rows y1 - y0).  vec: counts rows 16-byte aligned.
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_dftx_tc(const __half* __restrict__ counts, const uint4* __restrict__ Bhi,
+              const uint4* __restrict__ Blo, float2* __restrict__ X1, int Nx, int KT, int NT,
+              int nkx, int P_pad, int Ny, long long NR, int y0, int vec, uint32_t* st) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sA = sm;
+  unsigned char* sBh = sm + kTileA;
+  unsigned char* sBl = sm + kTileA + kTileB;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p0 = blockIdx.x * kM;
+  const int y = y0 + blockIdx.y;
+
+  if (warp == 0) tmem_alloc(&tmem_sh, kN);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  constexpr uint32_t idesc = make_idesc(kM, kN);
+  uint32_t phase = 0;
+
+  for (int nt = 0; nt < NT && !abort_sh; ++nt) {
+    for (int kt = 0; kt < KT; ++kt) {
+      // A tile: rows p0..p0+127, x = kt*64 .. +63 (zero outside the data)
+      for (int c = tid; c < kM * (kK / 8); c += kThreadsTC) {
+        const int r = c >> 3, kc = c & 7;
+        const int p = p0 + r, x = kt * kK + kc * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (p < P_pad) {
+          const __half* src = counts + (size_t)p * NR + (size_t)y * Nx + x;
+          if (vec && x + 8 <= Nx) {
+            v = __ldg(reinterpret_cast<const uint4*>(src));
+          } else {
+            __half h[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) h[i] = (x + i < Nx) ? src[i] : __float2half(0.f);
+            v = *reinterpret_cast<const uint4*>(h);
+          }
+        }
+        *reinterpret_cast<uint4*>(sA + cm_off(r, kc * 8)) = v;
+      }
+      // B tiles: contiguous pre-arranged blocks
+      const size_t tb = ((size_t)nt * KT + kt) * (kTileB / 16);
+      for (int c = tid; c < kTileB / 16; c += kThreadsTC) {
+        reinterpret_cast<uint4*>(sBh)[c] = __ldg(Bhi + tb + c);
+        reinterpret_cast<uint4*>(sBl)[c] = __ldg(Blo + tb + c);
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), bh0 = smem_u32(sBh), bl0 = smem_u32(sBl);
+#pragma unroll
+        for (int ks = 0; ks < kK / 16; ++ks) {
+          const uint64_t ad = make_desc(a0 + ks * 256);
+          mma_f16(tmem, ad, make_desc(bh0 + ks * 256), idesc, (kt | ks) != 0);
+          mma_f16(tmem, ad, make_desc(bl0 + ks * 256), idesc, 1u);
+        }
+        mma_commit(&mbar);
+      }
+      // the MMAs read the staged tiles: wait before they are overwritten
+      const bool ok = mbar_wait(&mbar, phase);
+      phase ^= 1u;
+      if (!ok) {
+        if (tid == 0) abort_sh = 1;
+        st_or(st, EER4D_ST_TIMEOUT);
+      }
+      __syncthreads();
+      if (abort_sh) break;
+    }
+    if (abort_sh) break;
+    // epilogue: accumulator columns -> X1 (column 2j re, 2j+1 im of k = nt*128 + j)
+    tc_fence_after();
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const int p = p0 + row;
+#pragma unroll 1
+    for (int j = 0; j < (kN / 2) / 16; ++j) {
+      const int col = half * (kN / 2) + j * 16;
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col, v);
+      if (p < P_pad) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = nt * (kN / 2) + (col >> 1) + i;
+          if (k < nkx) X1[((size_t)k * Ny + y) * P_pad + p] = make_float2(v[2 * i], v[2 * i + 1]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (abort_sh) mbar_wait(&mbar, phase ^ 1u);  // bounded: let an in-flight MMA retire
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kN);
+  }
+}
+
+}  // namespace
+
+// Host: the tile-blocked split DFT matrix for this plan's Nx.
+cudaError_t make_dftx_tc(eer4d_plan* p) {
+  const int Nx = p->g.scan_nx, nkx = p->nkx;
+  const int KT = (Nx + kK - 1) / kK;
+  const int NT = (2 * nkx + kN - 1) / kN;
+  const size_t tile_elems = (size_t)kN * kK;
+  std::vector<__half> hi((size_t)NT * KT * tile_elems), lo(hi.size());
+  const double tp = 6.283185307179586476925286766559;
+  for (int nt = 0; nt < NT; ++nt)
+    for (int kt = 0; kt < KT; ++kt) {
+      __half* th = hi.data() + ((size_t)nt * KT + kt) * tile_elems;
+      __half* tl = lo.data() + ((size_t)nt * KT + kt) * tile_elems;
+      for (int r = 0; r < kN; ++r)
+        for (int k = 0; k < kK; ++k) {
+          const int n = nt * kN + r, x = kt * kK + k, kx = n >> 1;
+          double w = 0.0;
+          if (x < Nx && kx < nkx) {
+            const long long e = ((long long)kx * x) % Nx;  // exact integer phase index
+            w = (n & 1) ? -sin(tp * (double)e / Nx) : cos(tp * (double)e / Nx);
+          }
+          const __half h = __float2half_rn((float)w);
+          const __half l = __float2half_rn((float)(w - (double)__half2float(h)));
+          const size_t o = ((size_t)(r >> 3) * 1024 + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2;
+          th[o] = h;
+          tl[o] = l;
+        }
+    }
+  cudaError_t e = cudaMalloc(&p->d_dft_hi, hi.size() * sizeof(__half));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&p->d_dft_lo, lo.size() * sizeof(__half));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(p->d_dft_hi, hi.data(), hi.size() * sizeof(__half), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(p->d_dft_lo, lo.data(), lo.size() * sizeof(__half), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
+                             uint32_t* st, cudaStream_t s) {
+  if (y1 <= y0) return cudaSuccess;
+  const int Nx = p->g.scan_nx, Ny = p->g.scan_ny;
+  const int KT = (Nx + kK - 1) / kK;
+  const int NT = (2 * p->nkx + kN - 1) / kN;
+  const long long NR = (long long)Ny * Nx;
+  const int vec = (Nx % 8 == 0) && (NR % 8 == 0);
+  const size_t smem = kTileA + 2 * kTileB;
+  cudaError_t e = ensure_smem((const void*)k_dftx_tc, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p->P_pad + kM - 1) / kM, y1 - y0);
+  stage_begin(p, EER4D_STAGE_DFT_X, s);
+  k_dftx_tc<<<grid, kThreadsTC, smem, s>>>(counts, reinterpret_cast<const uint4*>(p->d_dft_hi),
+                                           reinterpret_cast<const uint4*>(p->d_dft_lo), X1, Nx, KT,
+                                           NT, p->nkx, p->P_pad, Ny, NR, y0, vec, st);
+  count_launches(1);
+  stage_end(p, EER4D_STAGE_DFT_X, s);
+  return cudaGetLastError();
+}

@@ -317,3 +317,24 @@ def test_precision_workload_full_size(c2full):
     err = rel_l2(ph[0].cpu().numpy(), phi)
     print(f"precision workload FP32 SSB rel L2 = {err:.3e}")
     assert err <= 1e-5
+
+
+# ------------------------------------------ split-FP16 tensor-core DFT ------
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_split_fp16_dft_matches_fp32(which, request):
+    """The x-axis DFT on tcgen05 (counts exact in fp16, DFT factors split hi+lo,
+    FP32 accumulation) reproduces the FP32 FFT's G to 1e-6 of max|G| and the
+    SSB phase to 1e-4 relative L2 of the FP64 oracle."""
+    import paper_2104_06336_gb300 as P
+    c = request.getfixturevalue(which)
+    rec = P.Reconstructor(c.geom, precision=P.SPLIT_FP16)
+    rec.load(c.idx, c.off)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    Gt = rec.G_complex().cpu().numpy()
+    Gf = c.rec.G_complex().cpu().numpy()
+    assert np.abs(Gt - Gf).max() <= 1e-6 * np.abs(Gf).max()
+    ab = (80.0, 15.0, 25.98, 1.0e4, 0.0)
+    ph, var = rec.reconstruct(torch.tensor(ab, dtype=torch.float64))
+    phi, V = orc.ssb_phase(c.G_orc, c.geom, ab, "none")
+    assert rel_l2(ph[0].cpu().numpy(), phi) <= 1e-4
