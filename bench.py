@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--refocus-steps", type=int, default=220)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split"],
+                    help="scan DFT form: FP32 FFT or split-FP16 tensor-core DFT along x")
     return ap.parse_args()
 
 
@@ -220,7 +222,8 @@ def run_ours(args, rank, world, local_rank):
     d = synth.generate(w, dev)
     idx, off = d.idx.contiguous(), d.off.contiguous()
     C, F = idx.numel(), w.n_frames
-    rec = P.Reconstructor(geom, device=dev)
+    prec = P.SPLIT_FP16 if args.precision == "split" else P.FP32_FFT
+    rec = P.Reconstructor(geom, precision=prec, device=dev)
     Ny, nkx, P_pad = w.scan_ny, rec.info["nkx"], rec.info["P_pad"]
     theta = torch.zeros(5, dtype=torch.float64, device=dev)
     sums = torch.empty(3, F, dtype=torch.int64, device=dev)
@@ -299,7 +302,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "scan": [w.scan_ny, w.scan_nx], "detector": [w.det_h, w.det_w],
                    "bin": w.bin, "P": rec.info["P"], "events_per_gpu": C, "e_per_frame": w.e_per_frame,
-                   "precision": "FP32 FFT", "norm": "none", "sigma_K": sigma_k,
+                   "precision": "FP32 FFT" if args.precision == "fp32" else "split-FP16 tcgen05 DFT (x) + FP32 FFT (y)",
+                   "norm": "none", "sigma_K": sigma_k,
                    "l2": "inputs larger than L2 (events 4 B x C = %.0f MB; G %.2f GB); no flush" %
                          (4 * C / 1e6, 8 * P_pad * Ny * nkx / 1e9),
                    "parallelism": f"replicas x{world} (independent datasets, no collective)"},

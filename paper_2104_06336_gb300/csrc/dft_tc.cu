@@ -16,8 +16,10 @@
 // K = 16) and commits to an mbarrier; every wait on it is bounded by a
 // %globaltimer limit and, on expiry, sets EER4D_ST_TIMEOUT, stops issuing and
 // still frees the tensor memory.
+#include <cuda.h>
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -249,6 +251,175 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined form (TMA -> 2-stage shared ring -> tcgen05.mma -> double-buffered
+// TMEM accumulators -> epilogue warps), used when the TMA alignment rules hold
+// (Nx % 8 == 0, 16-byte aligned counts).  Warp 0 lane 0 is the producer: the
+// A tile (128 pixel rows x 64 frames of fp16 counts) by a 2D tensor-map load
+// with 128-byte swizzle, the pre-tiled B_hi / B_lo tiles by 1D bulk copies, all
+// completing on full[s].  Warp 1 lane 0 issues the MMAs and commits empty[s]
+// (stage free) and, per N tile, accf[b] (accumulator b ready).  Warps 4..7
+// drain accumulator b to X1 and arrive on acce[b].  Every wait is bounded.
+constexpr int kStages = 2;
+constexpr int kStageBytes = kTileA + 2 * kTileB;  // 80 KB, a multiple of 1024
+
+// K-major operand with 128-byte swizzle (rows of 64 fp16, 8-row atoms of
+// 1024 B): LBO unused (1), SBO 1024 B, layout type 2
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_dftx_tc2(const __grid_constant__ CUtensorMap tmA, const unsigned char* __restrict__ Bhi,
+               const unsigned char* __restrict__ Blo, float2* __restrict__ X1, int Nx, int KT,
+               int NT, int nlast, int nkx, int P_pad, int Ny, int y0, uint32_t* st) {
+  extern __shared__ unsigned char sm_raw[];
+  const uint32_t raw = smem_u32(sm_raw);
+  unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-aligned stages
+  __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ int wflag[kThreadsTC / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p0 = blockIdx.x * kM;
+  const int y = y0 + blockIdx.y;
+  if (warp == 2) tmem_alloc(&tmem_sh, 2 * kN);
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 4);
+    }
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const uint32_t idesc_full = make_idesc(kM, kN), idesc_last = make_idesc(kM, nlast);
+  const int total = NT * KT;
+
+  if (warp == 0 && lane == 0) {  // ---- producer
+    for (int it = 0; it < total && !abort_sh; ++it) {
+      const int s = it % kStages, k = it / kStages;
+      if (it >= kStages && !mbar_wait(&empty[s], (k - 1) & 1)) {
+        abort_sh = 1;
+        st_or(st, EER4D_ST_TIMEOUT);
+        break;
+      }
+      const int nt = it / KT, kt = it - nt * KT;
+      unsigned char* sa = sm + s * kStageBytes;
+      // the last N tile holds only nlast rows (a multiple of 16 = two 8-row groups)
+      const uint32_t bbytes = (uint32_t)((nt == NT - 1 ? nlast : kN) * kK * 2);
+      mbar_arrive_tx(&full[s], (uint32_t)kTileA + 2u * bbytes);
+      tma_load_2d(sa, &tmA, y * Nx + kt * kK, p0, &full[s]);
+      const size_t tb = ((size_t)nt * KT + kt) * kTileB;
+      bulk_load(sa + kTileA, Bhi + tb, bbytes, &full[s]);
+      bulk_load(sa + kTileA + kTileB, Blo + tb, bbytes, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {  // ---- MMA issuer
+    int it = 0;
+    for (int nt = 0; nt < NT && !abort_sh; ++nt) {
+      const int b = nt & 1, u = nt >> 1;
+      if (nt >= 2 && !mbar_wait(&acce[b], (u - 1) & 1)) {
+        abort_sh = 1;
+        st_or(st, EER4D_ST_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(b * kN);
+      for (int kt = 0; kt < KT; ++kt, ++it) {
+        const int s = it % kStages, k = it / kStages;
+        if (!mbar_wait(&full[s], k & 1)) {
+          abort_sh = 1;
+          st_or(st, EER4D_ST_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(sm + s * kStageBytes);
+        const uint32_t idesc = nt == NT - 1 ? idesc_last : idesc_full;
+#pragma unroll
+        for (int ks = 0; ks < kK / 16; ++ks) {
+          const uint64_t ad = make_desc_sw128(sa + ks * 32);
+          mma_f16(d, ad, make_desc(sa + kTileA + ks * 256), idesc, (kt | ks) != 0);
+          mma_f16(d, ad, make_desc(sa + kTileA + kTileB + ks * 256), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      if (abort_sh) break;
+      mma_commit(&accf[b]);
+    }
+  } else if (warp >= 4) {  // ---- epilogue
+    const int quarter = warp & 3;
+    const int p = p0 + quarter * 32 + lane;
+    for (int nt = 0; nt < NT; ++nt) {
+      const int b = nt & 1, u = nt >> 1;
+      if (lane == 0) {
+        const bool ok = !abort_sh && mbar_wait(&accf[b], u & 1);
+        if (!ok && !abort_sh) {
+          abort_sh = 1;
+          st_or(st, EER4D_ST_TIMEOUT);
+        }
+        wflag[warp] = ok;
+      }
+      __syncwarp();
+      if (!wflag[warp]) break;
+      tc_fence_after();
+      const uint32_t tb = tmem + (uint32_t)(b * kN) + ((uint32_t)(quarter * 32) << 16);
+      const int ncols = nt == NT - 1 ? nlast : kN;
+#pragma unroll 1
+      for (int j = 0; j < ncols / 16; ++j) {
+        float v[16];
+        tmem_ld16(tb + (uint32_t)(j * 16), v);
+        if (p < P_pad) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = nt * (kN / 2) + j * 8 + i;
+            if (k < nkx) X1[((size_t)k * Ny + y) * P_pad + p] = make_float2(v[2 * i], v[2 * i + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * kN);
+  }
+}
+
 }  // namespace
 
 // Host: the tile-blocked split DFT matrix for this plan's Nx.
@@ -287,6 +458,26 @@ cudaError_t make_dftx_tc(eer4d_plan* p) {
   return cudaMemcpy(p->d_dft_lo, lo.data(), lo.size() * sizeof(__half), cudaMemcpyHostToDevice);
 }
 
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+}  // namespace
+
 cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
                              uint32_t* st, cudaStream_t s) {
   if (y1 <= y0) return cudaSuccess;
@@ -294,6 +485,34 @@ cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* 
   const int KT = (Nx + kK - 1) / kK;
   const int NT = (2 * p->nkx + kN - 1) / kN;
   const long long NR = (long long)Ny * Nx;
+  // pipelined TMA form when its alignment rules hold: x coordinates (frames)
+  // at multiples of 8 fp16 (16 bytes), row stride NR*2 a multiple of 16
+  EncodeTiledFn enc = encode_fn();
+  if (enc && Nx % 8 == 0 && NR % 8 == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)NR, (cuuint64_t)p->P_pad};
+    const cuuint64_t gstride[1] = {(cuuint64_t)NR * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kK, (cuuint32_t)kM};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(counts), gdim, gstride,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+      const size_t smem = (size_t)kStages * kStageBytes + 1024;
+      cudaError_t e = ensure_smem((const void*)k_dftx_tc2, smem);
+      if (e != cudaSuccess) return e;
+      dim3 grid((p->P_pad + kM - 1) / kM, y1 - y0);
+      stage_begin(p, EER4D_STAGE_DFT_X, s);
+      const int rem = 2 * p->nkx - (NT - 1) * kN;  // columns of the last N tile
+      const int nlast = (rem + 15) / 16 * 16;
+      k_dftx_tc2<<<grid, kThreadsTC, smem, s>>>(
+          map, reinterpret_cast<const unsigned char*>(p->d_dft_hi),
+          reinterpret_cast<const unsigned char*>(p->d_dft_lo), X1, Nx, KT, NT, nlast, p->nkx,
+          p->P_pad, Ny, y0, st);
+      count_launches(1);
+      stage_end(p, EER4D_STAGE_DFT_X, s);
+      return cudaGetLastError();
+    }
+  }
   const int vec = (Nx % 8 == 0) && (NR % 8 == 0);
   const size_t smem = kTileA + 2 * kTileB;
   cudaError_t e = ensure_smem((const void*)k_dftx_tc, smem);
