@@ -223,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     idx, off = d.idx.contiguous(), d.off.contiguous()
     C, F = idx.numel(), w.n_frames
     prec = P.SPLIT_FP16 if args.precision == "split" else P.FP32_FFT
-    rec = P.Reconstructor(geom, precision=prec, device=dev)
+    rec = P.Reconstructor(geom, precision=prec, n_cand=64, device=dev)
     Ny, nkx, P_pad = w.scan_ny, rec.info["nkx"], rec.info["P_pad"]
     theta = torch.zeros(5, dtype=torch.float64, device=dev)
     sums = torch.empty(3, F, dtype=torch.int64, device=dev)
@@ -350,43 +350,56 @@ def run_ours(args, rank, world, local_rank):
                       "d2h_bytes_per_step": h_phase.numel() * 4 + 8,
                       "ms_per_step": float(e_ms.item())}
 
-    # ---- refocus: fused adjoint step replayed as a CUDA graph ----------------
+    # ---- refocus: adjoint step (CUDA graph) vs the plain form ----------------
     if args.refocus_steps > 0:
-        th = torch.zeros(5, dtype=torch.float64, device=dev)
-        stepv = torch.tensor([1e3, 1e3, 1e3, 0.0, 0.0], dtype=torch.float64, device=dev)
-        rv = torch.empty(1, dtype=torch.float64, device=dev)
-        rg = torch.empty(5, dtype=torch.float64, device=dev)
-        rph = torch.empty(Ny, w.scan_nx, dtype=torch.float32, device=dev)
-        s = torch.cuda.Stream(device=dev)
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            for _ in range(3):
-                P.ssb_refocus_step(rec.plan, rec.G, th, stepv, rec.scratch, rv, rg, rph, rec.status)
-        torch.cuda.current_stream().wait_stream(s)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            P.ssb_refocus_step(rec.plan, rec.G, th, stepv, rec.scratch, rv, rg, rph, rec.status)
+        rg = P.refocus.RefocusGraph(rec, [0.0] * 5, step=[1e-3, 1e-3, 1e-3, 0.0, 0.0])
         lat = []
         for _ in range(args.refocus_steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            g.replay()
+            rg.graph.replay()
             b.record()
             b.synchronize()
             lat.append(a.elapsed_time(b))
         lat.sort()
-        # plain form: one unbatched forward evaluation (trotter + inverse + variance)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(20):
-            P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var, status=rec.status)
-        b.record()
-        torch.cuda.synchronize()
-        out["refocus"] = {"ms_p50": lat[len(lat) // 2], "ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                          "replays": len(lat), "graph": True,
-                          "step": "V, dV/dtheta, phi and ascent update (one pass over G)",
-                          "forward_only_ms": a.elapsed_time(b) / 20}
+        cands = torch.zeros(64, 5, dtype=torch.float64, device=dev)
+        cands[:, 0] = torch.linspace(-200.0, 200.0, 64, dtype=torch.float64, device=dev)
+        ph64 = torch.empty(64, Ny, w.scan_nx, dtype=torch.float32, device=dev)
+        v64 = torch.empty(64, dtype=torch.float64, device=dev)
+
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        def plain_sweep():  # one unbatched forward (trotter + image + variance) per candidate
+            for i in range(64):
+                P.ssb_reconstruct(rec.plan, rec.G, cands[i], rec.scratch, phase, var, status=rec.status)
+
+        t_plain1 = timed(lambda: P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var,
+                                                   status=rec.status), reps=10)
+        t_plain64 = timed(plain_sweep)
+        t_b64v = timed(lambda: P.ssb_reconstruct(rec.plan, rec.G, cands, rec.scratch, None, v64,
+                                                 status=rec.status))
+        t_b64i = timed(lambda: P.ssb_reconstruct(rec.plan, rec.G, cands, rec.scratch, ph64, v64,
+                                                 status=rec.status))
+        out["refocus"] = {
+            "adjoint_step_ms_p50": lat[len(lat) // 2],
+            "adjoint_step_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "replays": len(lat), "graph": True,
+            "adjoint_step": "V, dV/dtheta, phase image and ascent update: one pass over G",
+            "plain_forward_ms": t_plain1,
+            "plain_sweep64_ms": t_plain64,
+            "batched_sweep64_var_ms": t_b64v,
+            "batched_sweep64_images_ms": t_b64i,
+            "phase_images_per_s": 64.0 / (t_b64i * 1e-3),
+        }
         rec.check()
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ---------

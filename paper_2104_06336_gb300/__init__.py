@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401  (C-ABI names)
 )
 from .pipeline import Reconstructor  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401
+from . import refocus  # noqa: F401
 
 
 def build(force: bool = False) -> str:
