@@ -60,6 +60,9 @@ extern "C" {
 /* ---- plan options ------------------------------------------------------- */
 #define EER4D_FP32_FFT   0  /* scan transform: FP32 radix FFT */
 #define EER4D_SPLIT_FP16 1  /* scan transform: split hi+lo FP16 DFT on tensor cores */
+#define EER4D_FP32_FFT_2PASS 2  /* FP32 radix FFT, always as two launches (x per chunk,
+                                   y at the end) through a full-size intermediate; the
+                                   same arithmetic as EER4D_FP32_FFT */
 #define EER4D_NORM_NONE  0  /* Eq. 3 as printed: S(K) = sum over K(K) */
 #define EER4D_NORM_AREA  1  /* S(K) / |K(K)| (0 when the set is empty) */
 
@@ -106,7 +109,7 @@ typedef struct eer4d_plan eer4d_plan;
 
 /* ---- plan ---------------------------------------------------------------- */
 /* Validates the geometry, builds the pixel, row and FFT tables on the current
- * device.  precision: EER4D_FP32_FFT or EER4D_SPLIT_FP16; norm:
+ * device.  precision: EER4D_FP32_FFT, EER4D_SPLIT_FP16 or EER4D_FP32_FFT_2PASS; norm:
  * EER4D_NORM_NONE or EER4D_NORM_AREA.  Returns EINVAL for an invalid
  * geometry (zero sizes, odd scan, crop_px < k0_px, more than 32767 kept
  * pixels, scan side > 4096), ENOMEM/ECUDA when the tables cannot be made. */
@@ -151,13 +154,19 @@ int com_dpc(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const
 /* ---- a4 + a5: bin/crop/densify and the G function (Table 1; Sec. IV) -------
  * Scatters frames [first_frame, first_frame + n_frames) into the counts at
  * the start of the workspace d_counts (fp16 [P_pad][scan_ny*scan_nx], exact
- * integers up to 2048), then runs the scan-axis DFT along x for every scan
- * row completed by this chunk into the second part of the workspace (at the
- * next 256-byte boundary: complex64 [scan_nx/2+1][scan_ny][P_pad]).  Chunks
- * must arrive in frame order starting at frame 0 (else EORDER).  With
- * is_last (the chunk ends at the last frame) the DFT along y completes
- * G(k, K) = F_{R->K} counts in d_G: complex64 [scan_nx/2+1][P_pad][scan_ny]
- * (K_x >= 0 half, K_y innermost; G(k,-K) = conj G(k,K)). */
+ * integers up to 2048; eer4d_workspace_bytes gives the workspace size).  The
+ * rest of the workspace (from the next 256-byte boundary) holds the
+ * intermediate of the scan DFT:
+ *  - FP32_FFT plans of square scans with side 128, 256, 512 or 1024: nothing
+ *    until is_last; then one persistent launch does both axes through a ring
+ *    of three pixel-group slabs kept in L2 and its task counters;
+ *  - otherwise: the DFT along x of every scan row completed by this chunk,
+ *    complex64 [scan_nx/2+1][scan_ny][P_pad]; with is_last the DFT along y.
+ * Chunks must arrive in frame order starting at frame 0 (else EORDER).  With
+ * is_last (the chunk ends at the last frame) d_G receives
+ * G(k, K) = F_{R->K} counts: complex64 [scan_nx/2+1][P_pad][scan_ny]
+ * (K_x >= 0 half, K_y innermost; G(k,-K) = conj G(k,K)).  The fused launch's
+ * bounded waits set EER4D_ST_TIMEOUT if they give up. */
 int ssb_accumulate(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
                    uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
                    int is_last, uint32_t* d_status, void* stream);
@@ -235,7 +244,8 @@ int ssb_reconstruct_static(const eer4d_plan* plan, const void* d_G, const double
 #define EER4D_STAGE_DFT_Y    5  /* scan DFT along y (ssb_accumulate, last chunk) */
 #define EER4D_STAGE_TROTTER  6  /* trotter integration / adjoint */
 #define EER4D_STAGE_IMAGE    7  /* variance and inverse transform to phi */
-#define EER4D_N_STAGES       8
+#define EER4D_STAGE_DFT_XY   8  /* fused scan DFT along x and y (ssb_accumulate, last chunk) */
+#define EER4D_N_STAGES       9
 /* When set, each stage records ev_start[s] before and ev_stop[s] after its
  * kernels on the launching stream.  The arrays hold EER4D_N_STAGES
  * cudaEvent_t owned by the caller (NULL entries are skipped); passing NULL

@@ -42,7 +42,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "pixel_table", "frame_of_events", "densify", "bin_crop_dense", "com_sums", "com_sums_dense",
+    "pixel_table", "frame_of_events", "event_pixels", "densify", "densify_pixels", "g_column",
+    "bin_crop_dense", "com_sums", "com_sums_dense",
     "pacbed", "pacbed_centre", "com_maps", "idpc", "g_function", "gbar0", "chi_turns",
     "kprime_f32", "kprime_f64", "trotter_mask", "ssb_spectrum", "ssb_phase", "ssb_grad",
     "variance", "ssb_value_and_grad_var", "fftfreq_index",
@@ -96,14 +97,12 @@ def _xy(idx, det_w):
 # Bin + crop + densify from linear-index EER (Table 1 rows "bin", "crop";
 # Sec. IV "densify the binned and cropped data")
 # --------------------------------------------------------------------------
-def densify(idx, off, geom) -> np.ndarray:
-    """counts[p][f] = number of events of frame f whose binned, cropped pixel is p.
-
-    Binned pixel u = floor((x - crop_x0) / bin), v likewise; events with an
-    index >= det_w*det_h, outside the binned window or outside the crop are
-    dropped."""
+def event_pixels(idx, off, geom):
+    """(p, f): the binned, cropped pixel (-1 when dropped) and the frame of
+    every event.  Binned pixel u = floor((x - crop_x0) / bin), v likewise;
+    events with an index >= det_w*det_h, outside the binned window or outside
+    the crop are dropped."""
     pt = pixel_table(geom)
-    F = len(off) - 1
     idx = np.asarray(idx, dtype=np.int64)
     f = frame_of_events(off)
     valid = idx < geom["det_w"] * geom["det_h"]
@@ -113,9 +112,32 @@ def densify(idx, off, geom) -> np.ndarray:
     inside = valid & (u >= 0) & (u < geom["pw"]) & (v >= 0) & (v < geom["ph"])
     p = np.full(idx.shape, -1, dtype=np.int64)
     p[inside] = pt["lut"][v[inside], u[inside]]
+    return p, f
+
+
+def densify(idx, off, geom) -> np.ndarray:
+    """counts[p][f] = number of events of frame f whose binned, cropped pixel is p."""
+    P = pixel_table(geom)["P"]
+    F = len(off) - 1
+    p, f = event_pixels(idx, off, geom)
     keep = p >= 0
-    flat = np.bincount(p[keep] * F + f[keep], minlength=pt["P"] * F)
-    return flat.reshape(pt["P"], F).astype(np.int64)
+    flat = np.bincount(p[keep] * F + f[keep], minlength=P * F)
+    return flat.reshape(P, F).astype(np.int64)
+
+
+def densify_pixels(idx, off, geom, pixels) -> np.ndarray:
+    """The rows ``pixels`` of densify (counts[i][f] of pixel pixels[i]) without
+    forming the others, for scans whose full count array does not fit."""
+    pixels = np.asarray(pixels, dtype=np.int64)
+    P = pixel_table(geom)["P"]
+    F = len(off) - 1
+    p, f = event_pixels(idx, off, geom)
+    row = np.full(P + 1, -1, dtype=np.int64)
+    row[pixels] = np.arange(len(pixels))
+    r = row[p]  # p = -1 maps to row[-1] = -1 (dropped)
+    keep = r >= 0
+    flat = np.bincount(r[keep] * F + f[keep], minlength=len(pixels) * F)
+    return flat.reshape(len(pixels), F).astype(np.int64)
 
 
 def bin_crop_dense(cube: np.ndarray, geom) -> np.ndarray:
@@ -224,6 +246,22 @@ def g_function(counts, geom) -> np.ndarray:
     Ny, Nx = geom["scan_ny"], geom["scan_nx"]
     c = np.asarray(counts, dtype=np.float64).reshape(-1, Ny, Nx)
     return np.fft.fft2(c, axes=(1, 2))
+
+
+def g_column(idx, off, geom, ky, kx) -> np.ndarray:
+    """G(p, K) for every pixel p at the one scan frequency K = (ky, kx) (DFT
+    bin indices), straight from the definition as a sum over events:
+    G(p, K) = sum over events e of pixel p of exp(-2 pi i (ky y_f/Ny + kx x_f/Nx)),
+    with (y_f, x_f) the raster position of the event's frame."""
+    Ny, Nx = geom["scan_ny"], geom["scan_nx"]
+    P = pixel_table(geom)["P"]
+    p, f = event_pixels(idx, off, geom)
+    keep = p >= 0
+    y, x = np.divmod(f[keep], Nx)
+    ph = -TWO_PI * (((ky * y) % Ny) / Ny + ((kx * x) % Nx) / Nx)
+    re = np.bincount(p[keep], weights=np.cos(ph), minlength=P)
+    im = np.bincount(p[keep], weights=np.sin(ph), minlength=P)
+    return re + 1j * im
 
 
 def gbar0(G, geom) -> float:

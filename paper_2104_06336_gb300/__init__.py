@@ -8,7 +8,7 @@ from . import _lib
 from ._lib import (  # noqa: F401  (C-ABI names)
     Plan, Eer4dError, eer_load_csr, com_dpc, ssb_accumulate, ssb_reconstruct, ssb_grad,
     ssb_variance_grad, ssb_trotter_counts, ssb_refocus_step, eer4d_set_stage_events,
-    eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, NORM_NONE, NORM_AREA,
+    eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, NORM_NONE, NORM_AREA,
 )
 from .pipeline import Reconstructor  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401

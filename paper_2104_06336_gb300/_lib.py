@@ -20,7 +20,7 @@ EER4D_EOVERFLOW, EER4D_ETIMEOUT, EER4D_ECUDA, EER4D_ENOMEM, EER4D_EORDER = -4, -
 EER4D_ESCRATCH = -9
 STATIC_SCRATCH_BYTES = 8 << 20
 ST_RANGE, ST_OFFSETS, ST_OVERFLOW, ST_TIMEOUT, ST_ROTATION = 0x1, 0x2, 0x4, 0x8, 0x10
-FP32_FFT, SPLIT_FP16 = 0, 1
+FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS = 0, 1, 2
 NORM_NONE, NORM_AREA = 0, 1
 
 EXPORTS = [
@@ -29,7 +29,7 @@ EXPORTS = [
     "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
 ]
-STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image"]
+STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image", "dft_xy"]
 
 
 class Geom(C.Structure):

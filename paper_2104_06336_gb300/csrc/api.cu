@@ -101,6 +101,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t work_counts_bytes(const eer4d_plan* p) { return (size_t)2 * p->P_pad * p->F; }
 size_t work_bytes(const eer4d_plan* p) {
+  if (dft2_fused_ok(p)) return al256(work_counts_bytes(p)) + al256(dft2_ring_bytes(p)) + dft2_ctl_bytes(p);
   return al256(work_counts_bytes(p)) + sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
 }
 
@@ -146,7 +147,9 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   if (!out) return EER4D_EINVAL;
   *out = nullptr;
   if (!geom_ok(h_geom)) return EER4D_EINVAL;
-  if (precision != EER4D_FP32_FFT && precision != EER4D_SPLIT_FP16) return EER4D_EINVAL;
+  if (precision != EER4D_FP32_FFT && precision != EER4D_SPLIT_FP16 &&
+      precision != EER4D_FP32_FFT_2PASS)
+    return EER4D_EINVAL;
   if (norm != EER4D_NORM_NONE && norm != EER4D_NORM_AREA) return EER4D_EINVAL;
   const eer4d_geom& g = *h_geom;
   eer4d_plan* p = static_cast<eer4d_plan*>(calloc(1, sizeof(eer4d_plan)));
@@ -332,6 +335,16 @@ int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
                                     d_status, s));
   if (rc != EER4D_OK) return rc;
   const uint64_t Nx = p->g.scan_nx;
+  if (dft2_fused_ok(p)) {  // both axes in one launch once every frame is in
+    p->next_frame = end;
+    if (is_last) {
+      unsigned char* ctl = reinterpret_cast<unsigned char*>(X1) + al256(dft2_ring_bytes(p));
+      rc = cuda_fail(launch_dft2_fused(p, counts, X1, G, reinterpret_cast<unsigned*>(ctl),
+                                       d_status, s));
+      p->next_frame = 0;
+    }
+    return rc;
+  }
   const int ya = (int)(first_frame / Nx), yb = (int)(end / Nx);
   rc = cuda_fail(p->precision == EER4D_SPLIT_FP16
                      ? launch_stage1_tc(p, counts, X1, ya, yb, d_status, s)

@@ -139,9 +139,16 @@ cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* 
 cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, int batch,
                              cudaStream_t s);
 // accumulation workspace of ssb_accumulate: fp16 counts [P_pad][F], then (at a
-// 256-byte boundary) the DFT-along-x intermediate complex64 [nkx][Ny][P_pad]
+// 256-byte boundary) either the DFT-along-x intermediate complex64
+// [nkx][Ny][P_pad], or, for plans that take the fused two-axis DFT, its ring of
+// three pixel-group slabs followed (at a 256-byte boundary) by its task counters
 size_t work_counts_bytes(const eer4d_plan* p);
 size_t work_bytes(const eer4d_plan* p);
+bool dft2_fused_ok(const eer4d_plan* p);
+size_t dft2_ring_bytes(const eer4d_plan* p);
+size_t dft2_ctl_bytes(const eer4d_plan* p);
+cudaError_t launch_dft2_fused(const eer4d_plan* p, const __half* counts, float2* ring, float2* G,
+                              unsigned* ctl, uint32_t* st, cudaStream_t s);
 cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam1, double lam2,
                         cudaStream_t s);
 cudaError_t launch_c2r_image(const eer4d_plan* p, float2* H, float* phase, int n_cand, cudaStream_t s);

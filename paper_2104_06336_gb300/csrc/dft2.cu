@@ -1,0 +1,260 @@
+// Fused two-axis scan DFT of the G function (Sec. IV: G(k, K) is the Fourier
+// transform of every detector pixel's image over the scan) for square
+// power-of-two scans, N = scan_ny = scan_nx in {128, 256, 512, 1024}.
+//
+// The separable transform runs as one persistent launch over a queue of
+// tiles.  Pixels are taken in groups of gp (8 or 16); for group g:
+//   S1 tasks (one per scan row y): real-to-complex DFT along x of the gp
+//      pixel rows at y, into ring slot g % 3, complex64 [nkx][N][gp];
+//   S2 tasks (one per K_x): DFT along y of the slot's gp columns at K_x,
+//      written transposed into G [nkx][P_pad][N]; the slot's lines are then
+//      dropped from L2 without write-back (discard.global.L2).
+// A slot is 8 pixels x N x (N/2 + 1) x 8 bytes (34 MB at N = 1024), so the
+// slots being written and read stay in the 126 MB L2: the DRAM traffic is
+// the fp16 counts read once and G written once, without the round trip of a
+// full-size intermediate.  Completion counts are published in batches (one
+// fence and atomic per CTA and change of group), the queue is read two tasks
+// ahead, and a CTA skips waits for groups it has already seen complete.  Tasks are handed out in the order S1(0), then
+// S1(g+1), S2(g) for g = 0, 1, ...; S2(g) waits until all S1(g) tasks are
+// done, S1(g) (g >= 3) until all S2(g-3) tasks are done (slot reuse).  Every
+// task waits only on tasks handed out before it, so the queue needs no
+// co-residency of CTAs.  Waits are bounded (1 s on %globaltimer and an
+// iteration cap); a wait that gives up sets EER4D_ST_TIMEOUT and an abort
+// flag that ends every CTA's loop.
+#include "fft_reg.cuh"
+
+namespace {
+
+#ifndef EER4D_DFT2_MINB
+#define EER4D_DFT2_MINB 4  // resident CTAs per SM the register budget is sized for
+#endif
+
+constexpr int kRing = 3;
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr unsigned kWaitIters = 1u << 24;
+
+struct Dft2Params {
+  int N, nkx, P_pad, gp, n_groups, n1, n2;
+  long long slot;   // float2 per ring slot
+  long long total;  // tasks
+  long long F;      // frames
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 only: waits until *cnt >= target.  False when the abort flag is set
+// or the wait gives up (then it sets EER4D_ST_TIMEOUT and the abort flag).
+__device__ bool wait_count(const unsigned* cnt, unsigned target, unsigned* abort_flag,
+                           uint32_t* st) {
+  if (ld_acquire(cnt) >= target) return true;
+  const unsigned long long t0 = now_ns();
+  for (unsigned it = 0; it < kWaitIters; ++it) {
+    __nanosleep(128);
+    if (ld_acquire(cnt) >= target) return true;
+    if (ld_acquire(abort_flag)) return false;
+    if (now_ns() - t0 > kWaitNs) break;
+  }
+  st_or(st, EER4D_ST_TIMEOUT);
+  atomicExch(abort_flag, 1u);
+  return false;
+}
+
+struct Task {
+  int type;  // 0 = S1 (DFT along x of one scan row), 1 = S2 (DFT along y)
+  int g;     // pixel group
+  int r;     // index within the group's tasks of that type
+};
+
+__device__ __forceinline__ Task decode(long long t, const Dft2Params& q) {
+  if (t < q.n1) return Task{0, 0, (int)t};
+  const long long u = t - q.n1;
+  const long long pair = (long long)q.n1 + q.n2;
+  const long long full = (long long)(q.n_groups - 1) * pair;
+  if (u < full) {
+    const int g = (int)(u / pair);
+    const int r = (int)(u - (long long)g * pair);
+    return r < q.n1 ? Task{0, g + 1, r} : Task{1, g, r - q.n1};
+  }
+  return Task{1, q.n_groups - 1, (int)(u - full)};
+}
+
+// Drops the L2 lines of [p, p + bytes) without writing them back (the slot
+// is dead once its S2 task has read it); p and bytes are multiples of 128.
+__device__ __forceinline__ void l2_discard(const void* p, size_t bytes, int tid, int nt) {
+  const size_t base = __cvta_generic_to_global(p);
+  for (size_t o = (size_t)tid * 128; o < bytes; o += (size_t)nt * 128)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + o) : "memory");
+}
+
+// Completion counts are published in batches: thread 0 holds the count of
+// finished tasks of one (type, group) and publishes it (fence, then one
+// atomic add) when its CTA moves to another (type, group), before any wait,
+// and at exit, always after a CTA barrier that follows the tasks it counts.
+struct Pending {
+  int type, g;
+  unsigned n;
+};
+
+__device__ __forceinline__ void publish(Pending& pd, unsigned* done1, unsigned* done2) {
+  if (pd.n) {
+    __threadfence();
+    atomicAdd((pd.type == 0 ? done1 : done2) + pd.g, pd.n);
+  }
+  pd.n = 0;
+  pd.type = pd.g = -1;
+}
+
+template <int R1, int R2, int CP>
+__global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
+    k_dft2_fused(const __half* __restrict__ counts, float2* ring, float2* G,
+                 const float2* __restrict__ twx, const float2* __restrict__ twy, Dft2Params q,
+                 unsigned* ctl, uint32_t* st) {
+  constexpr int NT = R1 * CP;
+  extern __shared__ float2 sm[];
+  __shared__ long long s_t[3];
+  __shared__ int s_ok;
+  unsigned* next = ctl;
+  unsigned* abort_flag = ctl + 1;
+  unsigned* done1 = ctl + 2;
+  unsigned* done2 = done1 + q.n_groups;
+  // thread 0's bookkeeping lives in shared memory (no registers in the tiles)
+  __shared__ Pending pd;
+  __shared__ int known1, known2;  // groups seen complete (S1, S2)
+  // The queue is read two tasks ahead: the index taken in iteration i is kept
+  // in a register and stored for iteration i + 2 only in iteration i + 1, so
+  // thread 0 never waits for the atomic's reply.
+  unsigned inflight = 0;
+  if (threadIdx.x == 0) {
+    pd.type = pd.g = -1;
+    pd.n = 0;
+    known1 = known2 = -1;
+    s_t[0] = atomicAdd(next, 1u);
+    s_t[1] = atomicAdd(next, 1u);
+  }
+  for (int it = 0;; ++it) {
+    __syncthreads();  // the previous task is finished by every thread
+    const long long t = s_t[it % 3];
+    if (t >= q.total) break;
+    const Task k = decode(t, q);
+    if (threadIdx.x == 0) {
+      if (it > 0) s_t[(it + 1) % 3] = inflight;
+      inflight = atomicAdd(next, 1u);
+      if (pd.n && (pd.type != k.type || pd.g != k.g)) publish(pd, done1, done2);
+      bool ok = true;
+      if (k.type == 1 && k.g > known1) {
+        publish(pd, done1, done2);
+        ok = wait_count(done1 + k.g, (unsigned)q.n1, abort_flag, st);
+        known1 = k.g;
+      } else if (k.type == 0 && k.g >= kRing && k.g - kRing > known2) {
+        publish(pd, done1, done2);
+        ok = wait_count(done2 + (k.g - kRing), (unsigned)q.n2, abort_flag, st);
+        known2 = k.g - kRing;
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    float2* slot = ring + (long long)(k.g % kRing) * q.slot;
+    const int p0 = k.g * q.gp;
+    if (k.type == 0) {
+      // S1: the gp pixel rows of scan row r, DFT along x into the slot
+      rowfft_r2c_tile<R1, R2, CP, true>(counts, slot, twx, q.P_pad, p0, p0, k.r, q.F, q.N,
+                                        (long long)q.N * q.gp, 1, q.gp, sm);
+    } else {
+      // S2: all gp pixel columns of K_x = r, DFT along y into G, CP at a time
+      const float2* blk = slot + (long long)k.r * q.N * q.gp;
+      float2* gout = G + ((long long)k.r * q.P_pad + p0) * q.N;
+      for (int c0 = 0; c0 < q.gp; c0 += CP) {
+        if (c0) __syncthreads();
+        colfft_tile<R1, R2, CP, 1, true, true>(blk, gout, twy, c0, q.gp, q.gp, q.N, 1.f, sm);
+      }
+      __syncthreads();
+      l2_discard(blk, sizeof(float2) * (size_t)q.N * q.gp, threadIdx.x, NT);
+    }
+    if (threadIdx.x == 0) {
+      pd.type = k.type;
+      pd.g = k.g;
+      ++pd.n;
+    }
+  }
+  if (threadIdx.x == 0) publish(pd, done1, done2);  // after the loop's last barrier
+}
+
+template <int R1, int R2, int CP>
+cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, float2* G,
+                     unsigned* ctl, size_t ctl_bytes, uint32_t* st, cudaStream_t s) {
+  constexpr int N = R1 * R2, NT = R1 * CP;
+  const size_t a = (size_t)R1 * CP * (R2 + 1) + 2 * CP, b = (size_t)N * CP;
+  const size_t sm = sizeof(float2) * (a > b ? a : b);
+  auto kern = k_dft2_fused<R1, R2, CP>;
+  cudaError_t e = ensure_smem((const void*)kern, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm)) != cudaSuccess)
+    return e;
+  Dft2Params q;
+  q.N = N;
+  q.nkx = p->nkx;
+  q.P_pad = p->P_pad;
+  q.gp = 2 * CP;
+  q.n_groups = p->P_pad / q.gp;
+  q.n1 = N;
+  q.n2 = p->nkx;
+  q.slot = (long long)p->nkx * N * q.gp;
+  q.total = (long long)q.n_groups * (q.n1 + q.n2);
+  q.F = (long long)N * N;
+  if ((e = cudaMemsetAsync(ctl, 0, ctl_bytes, s)) != cudaSuccess) return e;
+  long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+  if (grid > q.total) grid = q.total;
+  k_dft2_fused<R1, R2, CP><<<(unsigned)grid, NT, sm, s>>>(counts, ring, G, p->fx.tw, p->fy.tw, q,
+                                                          ctl, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dft2_fused_ok(const eer4d_plan* p) {
+  const int N = (int)p->g.scan_nx;
+  return p->precision == EER4D_FP32_FFT && p->g.scan_ny == p->g.scan_nx &&
+         (N == 128 || N == 256 || N == 512 || N == 1024);
+}
+
+static int dft2_gp(int N) { return N >= 512 ? 8 : 16; }
+
+size_t dft2_ring_bytes(const eer4d_plan* p) {
+  const int N = (int)p->g.scan_nx;
+  return sizeof(float2) * (size_t)kRing * p->nkx * N * dft2_gp(N);
+}
+
+size_t dft2_ctl_bytes(const eer4d_plan* p) {
+  const int n_groups = p->P_pad / dft2_gp((int)p->g.scan_nx);
+  return sizeof(unsigned) * (size_t)(2 + 2 * n_groups);
+}
+
+cudaError_t launch_dft2_fused(const eer4d_plan* p, const __half* counts, float2* ring, float2* G,
+                              unsigned* ctl, uint32_t* st, cudaStream_t s) {
+  const size_t cb = dft2_ctl_bytes(p);
+  stage_begin(p, EER4D_STAGE_DFT_XY, s);
+  cudaError_t e;
+  switch (p->g.scan_nx) {
+    case 1024: e = launch_t<32, 32, 4>(p, counts, ring, G, ctl, cb, st, s); break;
+    case 512: e = launch_t<32, 16, 4>(p, counts, ring, G, ctl, cb, st, s); break;
+    case 256: e = launch_t<16, 16, 8>(p, counts, ring, G, ctl, cb, st, s); break;
+    default: e = launch_t<16, 8, 8>(p, counts, ring, G, ctl, cb, st, s); break;
+  }
+  stage_end(p, EER4D_STAGE_DFT_XY, s);
+  return e;
+}

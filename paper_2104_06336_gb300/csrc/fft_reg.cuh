@@ -58,10 +58,13 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
         const float2 a = v[blk + j], b = v[blk + j + span];
         v[blk + j] = make_float2(a.x + b.x, a.y + b.y);
         const float2 d = make_float2(a.x - b.x, a.y - b.y);
+        const int m = j * (32 / (2 * span));  // twiddle exp(-+2 pi i m / 32)
         if (j == 0) {
           v[blk + j + span] = d;
+        } else if (m == 8) {  // -i (forward) or +i (inverse): a swap, no products
+          v[blk + j + span] = DIR > 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
         } else {
-          float2 w = w32(j * (32 / (2 * span)));
+          float2 w = w32(m);
           if (DIR < 0) w.y = -w.y;
           v[blk + j + span] = make_float2(d.x * w.x - d.y * w.y, d.x * w.y + d.y * w.x);
         }
@@ -86,32 +89,51 @@ __device__ __forceinline__ float2 twid_dir(const float2* __restrict__ tw, int e,
   return w;
 }
 
+// Global-memory access flavours of the tiles below: plain (L1 and L2), or
+// STREAM: the intermediate spectrum is read from L2 only (ld.global.cg; it may
+// have been written by another CTA of the same launch), the fp16 counts are
+// read once (ld.global.cs) and the G function is written once (st.global.cs),
+// so the L2 keeps the intermediate.
+template <bool STREAM>
+__device__ __forceinline__ float2 ld_f2(const float2* p) {
+  if (STREAM) return __ldcg(p);
+  return *p;
+}
+template <bool STREAM>
+__device__ __forceinline__ void st_f2(float2* p, float2 v) {
+  if (STREAM) __stcs(p, v);
+  else *p = v;
+}
+template <bool STREAM>
+__device__ __forceinline__ float ld_h(const __half* p) {
+  if (STREAM) return __half2float(__ldcs(p));
+  return __half2float(*p);
+}
+
 // Column transforms of a [N][ld] complex array (element n of column c at
-// n*ld_in + c), CB columns per CTA, batch = blockIdx.y.  Output element n of
+// n*ld_in + c), CB columns per CTA starting at column c0.  Output element n of
 // column c goes to n*ld_out + c, or with TOUT (transposed output) to
 // c*ld_out + n, so each column's spectrum is contiguous.  In place is allowed
 // only without TOUT (every input of the CTA is read before the barrier, every
-// output written after it, and CTAs own disjoint columns).
+// output written after it, and CTAs own disjoint columns).  All threads of the
+// CTA call it; `sm` holds R1*CB*(R2+1) + 2*CB float2.
 template <int R1, int R2, int CB, int DIR, bool TOUT>
 __device__ __forceinline__ int colfft_yidx(int k1, int col, int j2) {
   return TOUT ? ((col * R1 + k1) * (R2 + 1) + 2 * col + j2) : ((k1 * CB + col) * (R2 + 1) + j2);
 }
 
-template <int R1, int R2, int CB, int DIR, bool TOUT>
-__global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB)
-    k_colfft_reg(const float2* in, float2* out, const float2* __restrict__ tw, int ncols, int ld_in,
-                 int ld_out, long long bs_in, long long bs_out, float scale) {
-  constexpr int NT = (R1 > R2 ? R1 : R2) * CB;
-  extern __shared__ float2 sm[];
-  const int c0 = blockIdx.x * CB;
-  in += blockIdx.y * bs_in;
-  out += blockIdx.y * bs_out;
-  for (int g = threadIdx.x; g < R2 * CB; g += NT) {
+template <int R1, int R2, int CB, int DIR, bool TOUT, bool STREAM,
+          int NTH = (R1 > R2 ? R1 : R2) * CB>
+__device__ __forceinline__ void colfft_tile(const float2* in, float2* out,
+                                            const float2* __restrict__ tw, int c0, int ncols,
+                                            int ld_in, int ld_out, float scale, float2* sm) {
+  for (int g = threadIdx.x; g < R2 * CB; g += NTH) {
     const int col = g % CB, j2 = g / CB, c = c0 + col;
     float2 v[R1];
 #pragma unroll
     for (int j1 = 0; j1 < R1; ++j1)
-      v[j1] = c < ncols ? in[(size_t)(R2 * j1 + j2) * ld_in + c] : make_float2(0.f, 0.f);
+      v[j1] = c < ncols ? ld_f2<STREAM>(in + (size_t)(R2 * j1 + j2) * ld_in + c)
+                        : make_float2(0.f, 0.f);
     dft_reg<R1, DIR>(v);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB)
     }
   }
   __syncthreads();
-  for (int g = threadIdx.x; g < R1 * CB; g += NT) {
+  for (int g = threadIdx.x; g < R1 * CB; g += NTH) {
     int col, k1;
     if (TOUT) { k1 = g % R1; col = g / R1; } else { col = g % CB; k1 = g / CB; }
     const int c = c0 + col;
@@ -129,45 +151,65 @@ __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB)
     for (int j2 = 0; j2 < R2; ++j2) v[j2] = sm[colfft_yidx<R1, R2, CB, DIR, TOUT>(k1, col, j2)];
     dft_reg<R2, DIR>(v);
     if (c < ncols) {
+      if (scale != 1.f) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k2] = make_float2(v[k2].x * scale, v[k2].y * scale);
+      }
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) {
         const int n = k1 + R1 * k2;
         const size_t o = TOUT ? (size_t)c * ld_out + n : (size_t)n * ld_out + c;
-        out[o] = make_float2(v[k2].x * scale, v[k2].y * scale);
+        st_f2<STREAM>(out + o, v[k2]);
       }
     }
   }
 }
 
+// CTA x covers columns [x*CB, x*CB + CB), batch = blockIdx.y.
+template <int R1, int R2, int CB, int DIR, bool TOUT>
+__global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB, 768 / ((R1 > R2 ? R1 : R2) * CB))
+    k_colfft_reg(const float2* in, float2* out, const float2* __restrict__ tw, int ncols, int ld_in,
+                 int ld_out, long long bs_in, long long bs_out, float scale) {
+  extern __shared__ float2 sm[];
+  colfft_tile<R1, R2, CB, DIR, TOUT, false>(in + blockIdx.y * bs_in, out + blockIdx.y * bs_out, tw,
+                                           blockIdx.x * CB, ncols, ld_in, ld_out, scale, sm);
+}
+
 // Real rows (fp16 counts) -> half spectra, scan DFT along x of the G function.
 // Row (a, c) = (pixel, scan row y) starts at a*in_sa + c*in_sc; spectrum value
-// k goes to k*out_skx + a*out_sa + c*out_sc.  A CTA takes 2*CP consecutive
-// pixels at one y and transforms them as CP complex rows z = row_2b + i
-// row_2b+1; A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2.
-// Requires R1 >= R2 so pass 2 has exactly one (k1, b) group per thread.
-template <int R1, int R2, int CP>
-__global__ void __launch_bounds__(R1 * CP)
-    k_rowfft_r2c_reg(const __half* __restrict__ in, float2* out, const float2* __restrict__ tw,
-                     int nA, int c0, long long in_sa, long long in_sc, long long out_skx,
-                     long long out_sa, long long out_sc) {
+// k goes to k*out_skx + (a - a_out0)*out_sa + c*out_sc.  The tile takes 2*CP
+// consecutive pixels from a0 at scan row c and transforms them as CP complex
+// rows z = row_2b + i row_2b+1; A(k) = (Z(k) + conj Z(-k))/2,
+// B(k) = -i (Z(k) - conj Z(-k))/2.  Requires R1 >= R2 so pass 2 has exactly
+// one (k1, b) group per thread.  `sm` holds max(R1*CP*(R2+1), N*CP) float2.
+template <int R1, int R2, int CP, bool STREAM>
+__device__ __forceinline__ void rowfft_r2c_tile(const __half* __restrict__ in, float2* out,
+                                                const float2* __restrict__ tw, int nA, int a0,
+                                                int a_out0, int c, long long in_sa,
+                                                long long in_sc, long long out_skx,
+                                                long long out_sa, long long out_sc, float2* sm) {
   static_assert(R1 >= R2, "R1 >= R2");
   constexpr int N = R1 * R2;
   constexpr int NT = R1 * CP;
   constexpr int PITCH = R2 + 1;
-  extern __shared__ float2 sm[];
-  const int a0 = blockIdx.x * 2 * CP;
-  const int c = c0 + blockIdx.y;
+  const bool full = a0 + 2 * CP <= nA;  // every pixel row of the tile exists
   for (int g = threadIdx.x; g < R2 * CP; g += NT) {
     const int j2 = g % R2, b = g / R2;
     const int ra = a0 + 2 * b, rb = ra + 1;
     const __half* pa = in + ra * in_sa + c * in_sc + j2;
     const __half* pb = in + rb * in_sa + c * in_sc + j2;
     float2 v[R1];
+    if (full) {
 #pragma unroll
-    for (int j1 = 0; j1 < R1; ++j1) {
-      const float xa = ra < nA ? __half2float(pa[R2 * j1]) : 0.f;
-      const float xb = rb < nA ? __half2float(pb[R2 * j1]) : 0.f;
-      v[j1] = make_float2(xa, xb);
+      for (int j1 = 0; j1 < R1; ++j1)
+        v[j1] = make_float2(ld_h<STREAM>(pa + R2 * j1), ld_h<STREAM>(pb + R2 * j1));
+    } else {
+#pragma unroll
+      for (int j1 = 0; j1 < R1; ++j1) {
+        const float xa = ra < nA ? ld_h<STREAM>(pa + R2 * j1) : 0.f;
+        const float xb = rb < nA ? ld_h<STREAM>(pb + R2 * j1) : 0.f;
+        v[j1] = make_float2(xa, xb);
+      }
     }
     dft_reg<R1, 1>(v);
 #pragma unroll
@@ -188,17 +230,35 @@ __global__ void __launch_bounds__(R1 * CP)
     for (int k2 = 0; k2 < R2; ++k2) sm[(k1 + R1 * k2) * CP + b] = v[k2];
   }
   __syncthreads();
+  // one thread per (k, pair b): both half spectra from Z(k) and Z(-k).  With
+  // out_sa == 1 the pair's two values are adjacent and go out as one 16-byte
+  // store (callers keep out, out_skx, out_sc and a0 - a_out0 even).
   constexpr int NK = N / 2 + 1;
-  for (int w = threadIdx.x; w < NK * 2 * CP; w += NT) {
-    const int i = w % (2 * CP), k = w / (2 * CP);
-    const int a = a0 + i;
+  for (int w = threadIdx.x; w < NK * CP; w += NT) {
+    const int b = w % CP, k = w / CP;
+    const int a = a0 + 2 * b;
     if (a >= nA) continue;
-    const int b = i >> 1;
     const float2 z = sm[k * CP + b];
     const float2 zm = sm[((N - k) & (N - 1)) * CP + b];
-    float2 r;
-    if ((i & 1) == 0) r = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-    else r = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-    out[k * out_skx + a * out_sa + c * out_sc] = r;
+    const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+    float2* o = out + k * out_skx + (a - a_out0) * out_sa + c * out_sc;
+    if (out_sa == 1 && a + 1 < nA) {
+      *reinterpret_cast<float4*>(o) = make_float4(A.x, A.y, B.x, B.y);
+    } else {
+      o[0] = A;
+      if (a + 1 < nA) o[out_sa] = B;
+    }
   }
+}
+
+// CTA (x, y) takes pixels [2*CP*x, 2*CP*x + 2*CP) at scan row c0 + y.
+template <int R1, int R2, int CP>
+__global__ void __launch_bounds__(R1 * CP, 768 / (R1 * CP))
+    k_rowfft_r2c_reg(const __half* __restrict__ in, float2* out, const float2* __restrict__ tw,
+                     int nA, int c0, long long in_sa, long long in_sc, long long out_skx,
+                     long long out_sa, long long out_sc) {
+  extern __shared__ float2 sm[];
+  rowfft_r2c_tile<R1, R2, CP, false>(in, out, tw, nA, blockIdx.x * 2 * CP, 0, c0 + blockIdx.y,
+                                     in_sa, in_sc, out_skx, out_sa, out_sc, sm);
 }

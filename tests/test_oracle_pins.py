@@ -94,6 +94,39 @@ def test_g_function_parseval_rectangular():
     np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
 
 
+def test_densify_pixels_are_rows_of_the_dense_path():
+    """The sampled-pixel densify equals the dense-format binning (Table 1) on
+    the chosen rows, including the first and last pixel and repeats of none."""
+    w = synth.workload(1)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    geom = synth.geometry(w)
+    cube = _dense_cube(idx, off, w.det_w, w.det_h, np.int32)
+    dense = orc.bin_crop_dense(cube, geom)
+    P = dense.shape[0]
+    sel = np.array([0, 7, P // 2, P - 2, P - 1])
+    np.testing.assert_array_equal(orc.densify_pixels(idx, off, geom, sel), dense[sel])
+
+
+def test_g_column_equals_brute_force_sum():
+    """G(p, K) at single scan frequencies from the event sum equals the DFT
+    written as an explicit sum over scan positions of the dense-path counts."""
+    w = synth.workload(1)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    geom = synth.geometry(w)
+    Ny, Nx = w.scan_ny, w.scan_nx
+    dense = orc.bin_crop_dense(_dense_cube(idx, off, w.det_w, w.det_h, np.int32), geom)
+    c = dense.reshape(-1, Ny, Nx).astype(np.float64)
+    y = np.arange(Ny)[:, None]
+    x = np.arange(Nx)[None, :]
+    for ky, kx in [(0, 0), (1, 0), (0, 3), (5, 7), (Ny // 2, Nx // 2), (Ny - 1, 1)]:
+        e = np.cos(2 * math.pi * (ky * y / Ny + kx * x / Nx)) - 1j * np.sin(2 * math.pi * (ky * y / Ny + kx * x / Nx))
+        ref = (c * e[None]).sum(axis=(1, 2))
+        got = orc.g_column(idx, off, geom, ky, kx)
+        assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
 # ------------------------------------------------------------------- COM ---
 @pytest.mark.parametrize("g", [(3, -2), (0, 5), (-4, -4)])
 def test_com_of_phase_ramp_is_its_tilt(g):
