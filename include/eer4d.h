@@ -214,6 +214,26 @@ int ssb_refocus_step(const eer4d_plan* plan, const void* d_G, double* d_aberr, c
                      void* d_scratch, float* d_phase, double* d_var, double* d_grad,
                      uint32_t* d_status, void* stream);
 
+/* ---- several datasets in one launch (Sec. IV, S(K) of Eq. 3 per dataset) -----
+ * Uneven batches: n_sets (1..EER4D_MAX_SETS) datasets recorded with one
+ * detector geometry (identical det_w, det_h, bin, crop, aperture, wavelength
+ * and pixel angle; the scans and doses may differ) are reconstructed by one
+ * persistent trotter launch over the bins of all of them, then one variance
+ * reduction over all and each dataset's inverse transform.  h_plans[i] (host
+ * array) is dataset i's plan and h_G[i] (host array of device pointers) its G
+ * from ssb_accumulate; d_aberr is double [n_sets][5], row i the aberrations
+ * (and scan rotation) of dataset i.  Outputs: h_phase[i] (host array of device
+ * pointers, the array or any entry NULL to skip) float [scan_ny_i][scan_nx_i];
+ * d_var double [n_sets] (nullable).  d_scratch needs the bytes
+ * eer4d_batched_scratch_bytes returns.  EINVAL when n_sets is out of range, a
+ * pointer is NULL or the detector geometries differ.  Stage events, if any,
+ * are those of h_plans[0]. */
+#define EER4D_MAX_SETS 32
+int eer4d_batched_scratch_bytes(const eer4d_plan* const* h_plans, int n_sets, size_t* h_bytes);
+int ssb_reconstruct_batched(const eer4d_plan* const* h_plans, const void* const* h_G, int n_sets,
+                            const double* d_aberr, void* d_scratch, float* const* h_phase,
+                            double* d_var, uint32_t* d_status, void* stream);
+
 /* ---- reconstruction without scratch allocation --------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory where they want an image (a host application

@@ -28,7 +28,9 @@ EXPORTS = [
     "eer4d_status_code", "eer4d_strerror", "eer4d_last_error", "eer_load_csr", "com_dpc",
     "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
+    "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched",
 ]
+MAX_SETS = 32
 STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image", "dft_xy"]
 
 
@@ -92,6 +94,8 @@ def load(path: str | None = None):
         "eer4d_set_stage_events": (I32, [P, P, P]),
         "eer4d_launch_count": (C.c_uint64, []),
         "ssb_reconstruct_static": (I32, [P, P, P, P, P, P, P]),
+        "eer4d_batched_scratch_bytes": (I32, [P, I32, C.POINTER(S)]),
+        "ssb_reconstruct_batched": (I32, [P, P, I32, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -240,3 +244,35 @@ def ssb_reconstruct_static(plan: Plan, G, aberr, phase=None, var=None, status=No
     _check(load().ssb_reconstruct_static(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
                                          _ptr(phase, "phase"), _ptr(var, "var"),
                                          _ptr(status, "status"), _stream()), "ssb_reconstruct_static")
+
+
+def _handles(plans):
+    arr = (C.c_void_p * len(plans))(*[p.handle for p in plans])
+    return arr
+
+
+def batched_scratch_bytes(plans) -> int:
+    n = C.c_size_t(0)
+    _check(load().eer4d_batched_scratch_bytes(_handles(plans), len(plans), C.byref(n)),
+           "eer4d_batched_scratch_bytes")
+    return int(n.value)
+
+
+def ssb_reconstruct_batched(plans, Gs, aberr, scratch, phases=None, var=None, status=None):
+    """Datasets of one detector geometry in one trotter launch: plans and Gs
+    are lists (one per dataset), aberr [n][5] float64 on the device, phases a
+    list of [Ny_i][Nx_i] float32 tensors (or None entries) or None."""
+    n = len(plans)
+    if len(Gs) != n or aberr.numel() != 5 * n:
+        raise ValueError("one G and one aberration row per plan")
+    g_arr = (C.c_void_p * n)(*[_ptr(g, "G").value for g in Gs])
+    ph_arr = None
+    if phases is not None:
+        if len(phases) != n:
+            raise ValueError("one phase output (or None) per plan")
+        ph_arr = (C.c_void_p * n)(*[(_ptr(ph, "phase").value if ph is not None else None)
+                                    for ph in phases])
+    _check(load().ssb_reconstruct_batched(_handles(plans), g_arr, n, _ptr(aberr, "aberr"),
+                                          _ptr(scratch, "scratch"), ph_arr, _ptr(var, "var"),
+                                          _ptr(status, "status"), _stream()),
+           "ssb_reconstruct_batched")

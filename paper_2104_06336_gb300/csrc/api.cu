@@ -399,6 +399,44 @@ int ssb_refocus_step(const eer4d_plan* p, const void* d_G, double* d_aberr, cons
   return cuda_fail(launch_ascent(d_aberr, d_step, d_grad, s));
 }
 
+static bool same_detector(const eer4d_plan* a, const eer4d_plan* b) {
+  const eer4d_geom &x = a->g, &y = b->g;
+  return x.det_w == y.det_w && x.det_h == y.det_h && x.bin == y.bin && x.crop_x0 == y.crop_x0 &&
+         x.crop_y0 == y.crop_y0 && x.pw == y.pw && x.ph == y.ph && x.dc_u == y.dc_u &&
+         x.dc_v == y.dc_v && x.k0_px == y.k0_px && x.crop_px == y.crop_px &&
+         x.lambda_A == y.lambda_A && x.dalpha_rad == y.dalpha_rad && a->P == b->P &&
+         a->P_pad == b->P_pad && a->P_bf == b->P_bf;
+}
+
+static int check_batch(const eer4d_plan* const* plans, int n) {
+  if (!plans || n < 1 || n > EER4D_MAX_SETS) return EER4D_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!plans[i] || !same_detector(plans[0], plans[i])) return EER4D_EINVAL;
+  return EER4D_OK;
+}
+
+int eer4d_batched_scratch_bytes(const eer4d_plan* const* plans, int n, size_t* bytes) {
+  const int rc = check_batch(plans, n);
+  if (rc != EER4D_OK || !bytes) return rc != EER4D_OK ? rc : EER4D_EINVAL;
+  *bytes = trotter_batched_scratch_bytes(plans, n);
+  return EER4D_OK;
+}
+
+int ssb_reconstruct_batched(const eer4d_plan* const* plans, const void* const* d_G, int n,
+                            const double* d_aberr, void* d_scratch, float* const* d_phase,
+                            double* d_var, uint32_t* d_status, void* stream) {
+  int rc = check_batch(plans, n);
+  if (rc != EER4D_OK) return rc;
+  if (!d_G || !d_aberr || !d_scratch) return EER4D_EINVAL;
+  const float2* G[EER4D_MAX_SETS];
+  for (int i = 0; i < n; ++i) {
+    if (!d_G[i]) return EER4D_EINVAL;
+    G[i] = static_cast<const float2*>(d_G[i]);
+  }
+  return cuda_fail(launch_trotter_batched(plans, G, n, d_aberr, d_scratch, d_phase, d_var,
+                                          d_status, (cudaStream_t)stream));
+}
+
 int ssb_trotter_counts(const eer4d_plan* p, const double* d_aberr, int32_t* d_count,
                        void* d_scratch, void* stream) {
   if (!p || !d_aberr || !d_count || !d_scratch) return EER4D_EINVAL;

@@ -157,6 +157,10 @@ cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cud
 // trotter modes
 enum { TROT_FWD = 0, TROT_GRAD = 1, TROT_VARGRAD = 2, TROT_COUNT = 3 };
 cudaError_t launch_ascent(double* theta, const double* step, const double* grad, cudaStream_t s);
+size_t trotter_batched_scratch_bytes(const eer4d_plan* const* plans, int n);
+cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2* const* G, int n,
+                                   const double* aberr, void* scratch, float* const* phase,
+                                   double* var, uint32_t* st, cudaStream_t s);
 size_t trotter_scratch_bytes(const eer4d_plan* p, int n_cand, int mode);
 cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* aberr, int n_cand,
                            int mode, void* scratch, const float2* W, float* phase_out,

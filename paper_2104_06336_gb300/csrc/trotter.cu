@@ -53,9 +53,12 @@ __device__ __forceinline__ float chi_turns(const CandCoef& c, float qx, float qy
 }
 
 // Candidate coefficients and per-pixel exp(-i chi(k_p)).
+// own_rot: every row uses its own rotation (independent datasets); otherwise
+// the mask rotation of all candidates is that of row 0 and a different
+// rotation in another row is flagged.
 __global__ void k_prep(const double* __restrict__ aberr, int n_cand, const short2* __restrict__ pix,
                        int P_pad, int P, double dalpha, double lambda, CandCoef* coef, float2* ek,
-                       uint32_t* st) {
+                       uint32_t* st, int own_rot = 0) {
   __shared__ CandCoef sc;
   const int c = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -66,14 +69,15 @@ __global__ void k_prep(const double* __restrict__ aberr, int n_cand, const short
     k.a2 = (float)(a[1] * d2 / (2.0 * lambda));
     k.a3 = (float)(a[2] * d2 / lambda);
     k.a4 = (float)(a[3] * d2 * d2 / (4.0 * lambda));
-    k.c = (float)cos(aberr[4]);  // the mask rotation is that of candidate 0
-    k.s = (float)sin(aberr[4]);
+    const double rot = own_rot ? a[4] : aberr[4];
+    k.c = (float)cos(rot);
+    k.s = (float)sin(rot);
     const double tp = 6.283185307179586476925;
     k.u1 = (float)(tp * d2 / (2.0 * lambda));
     k.u3 = (float)(tp * d2 / lambda);
     k.u4 = (float)(tp * d2 * d2 / (4.0 * lambda));
     k.pad[0] = k.pad[1] = k.pad[2] = 0.f;
-    if (a[4] != aberr[4]) st_or(st, EER4D_ST_ROTATION);
+    if (!own_rot && a[4] != aberr[4]) st_or(st, EER4D_ST_ROTATION);
     sc = k;
     coef[c] = k;
   }
@@ -346,6 +350,189 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TRO
   }
 }
 
+// ---- several datasets of one detector geometry in one launch ---------------
+// Every dataset s has its own scan (Ny, Nx), G, aberrations (row s of the
+// candidates) and output spectrum H_s; the bright-field pixel table is shared.
+// The warp tasks of all datasets are numbered one after another (task0 is the
+// first of dataset s) and the persistent grid walks them all, so small scans
+// fill the GPU together.  Same per-bin arithmetic, in the same pixel order, as
+// the single-dataset kernel with one candidate.
+constexpr int kMaxSets = EER4D_MAX_SETS;
+
+struct SetDesc {
+  const float2* G;
+  float2* H;
+  int Ny, Nx, nkx, norm;
+  float kpm_x, kpm_y;
+  int task0;
+  float NR;
+};
+
+struct BatchParams {
+  int n_sets, P_pad, P_bf, ntask;
+  float k0sq;
+  SetDesc s[kMaxSets];
+};
+
+__global__ void k_gbar_batched(const __grid_constant__ BatchParams B, const int32_t* __restrict__ bfp,
+                               double* gscale) {
+  __shared__ double red[256];
+  const SetDesc& D = B.s[blockIdx.x];
+  double sum = 0.0;
+  for (int q = threadIdx.x; q < B.P_bf; q += blockDim.x) sum += (double)D.G[(size_t)bfp[q] * D.Ny].x;
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double g0 = B.P_bf ? red[0] / (double)B.P_bf : 0.0;
+    gscale[2 * blockIdx.x] = g0;
+    gscale[2 * blockIdx.x + 1] = g0 != 0.0 ? (double)D.NR / g0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 3)
+    k_trotter_batched(const __grid_constant__ BatchParams B, const int32_t* __restrict__ bfp,
+                      const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
+                      const float2* __restrict__ ek, const double* __restrict__ gscale) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* skk = reinterpret_cast<float2*>(smem_raw);  // [P_bf] (kx, ky)
+  int* sp = reinterpret_cast<int*>(skk + B.P_bf);     // [P_bf] kept-pixel index
+  for (int q = threadIdx.x; q < B.P_bf; q += blockDim.x) {
+    const int p = bfp[q];
+    const short2 k = pix[p];
+    skk[q] = make_float2((float)k.x, (float)k.y);
+    sp[q] = p;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + warp;
+  const int nwarps = gridDim.x * kWarps;
+  int si = 0;
+  for (int t = gw; t < B.ntask; t += nwarps) {
+    while (si + 1 < B.n_sets && t >= B.s[si + 1].task0) ++si;  // tasks only grow
+    const SetDesc& D = B.s[si];
+    const CandCoef cf = coef[si];
+    const float2* eks = ek + (size_t)si * B.P_pad;
+    const float scale = (float)gscale[2 * si + 1];
+    const int tl = t - D.task0;
+    const int nyw = (D.Ny + 31) >> 5;
+    const int mx = tl / nyw;
+    const int my0 = (tl - mx * nyw) * 32;
+    const int my = my0 + lane;
+    const bool active = my < D.Ny;
+    const int mys = active ? my : 0;
+    const int mmx = (D.Nx - mx) % D.Nx, mmy = (D.Ny - mys) % D.Ny;
+    float Kpx, Kpy, Kmx, Kmy;
+    kprime(cf, D.kpm_x, D.kpm_y, freq_index(mx, D.Nx), freq_index(mys, D.Ny), Kpx, Kpy);
+    kprime(cf, D.kpm_x, D.kpm_y, freq_index(mmx, D.Nx), freq_index(mmy, D.Ny), Kmx, Kmy);
+    const bool nyq = (2 * mx == D.Nx) || (2 * mys == D.Ny);
+    const bool nyq_warp = (2 * mx == D.Nx) || (D.Ny / 2 >= my0 && D.Ny / 2 < my0 + 32);
+    const float2* Gl = D.G + (size_t)mx * B.P_pad * D.Ny + mys;
+    float2 SP = make_float2(0.f, 0.f), SM = make_float2(0.f, 0.f);
+    int nP = 0, nM = 0;
+    auto contrib = [&](float2 g, float Kx, float Ky, float2 kk, int q, float wp) {
+      const float qx = kk.x - Kx, qy = kk.y - Ky;
+      const float wm = 1.f - wp;
+      const float tq = chi_turns(cf, qx, qy);
+      const float fr = tq - rintf(tq);
+      float sn, cs;
+      __sincosf(kTwoPi * fr, &sn, &cs);
+      const float2 e = __ldg(eks + sp[q]);
+      const float2 ph = make_float2(e.x * cs - e.y * sn, e.x * sn + e.y * cs);
+      const float2 term = cmul(g, ph);
+      SP = cmadd(SP, term, wp);
+      SM = cmadd(SM, term, wm);
+    };
+    for (int q0 = 0; q0 < B.P_bf; q0 += kBatch) {
+      unsigned mP = 0u, mM = 0u;
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        const int q = q0 + i;
+        if (q >= B.P_bf) break;
+        const float2 kk = skk[q];
+        const float dm = dist2(kk.x, kk.y, Kpx, Kpy);
+        const float dp = dist2(kk.x, kk.y, -Kpx, -Kpy);
+        const bool memP = active && dm < B.k0sq && dp > B.k0sq;
+        bool memM;
+        if (!nyq) {
+          memM = active && dp < B.k0sq && dm > B.k0sq;
+        } else {
+          const float em = dist2(kk.x, kk.y, Kmx, Kmy);
+          const float ep = dist2(kk.x, kk.y, -Kmx, -Kmy);
+          memM = active && em < B.k0sq && ep > B.k0sq;
+        }
+        mP |= (unsigned)memP << i;
+        mM |= (unsigned)memM << i;
+      }
+      nP += __popc(mP);
+      nM += __popc(mM);
+      const unsigned mAny = mP | mM;
+      if (mAny == 0u) continue;
+      float2 gb[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        gb[i] = ((mAny >> i) & 1u) ? Gl[(size_t)sp[q0 + i] * D.Ny] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) {
+        const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
+        if (!(memP || memM)) continue;
+        const int q = q0 + i;
+        const float2 kk = skk[q];
+        const float2 g = gb[i];
+        if (!nyq_warp) {
+          const float2 gg = memM ? make_float2(g.x, -g.y) : g;
+          contrib(gg, memM ? Kmx : Kpx, memM ? Kmy : Kpy, kk, q, memM ? 0.f : 1.f);
+        } else {
+          if (memP) contrib(g, Kpx, Kpy, kk, q, 1.f);
+          if (memM) contrib(make_float2(g.x, -g.y), Kmx, Kmy, kk, q, 0.f);
+        }
+      }
+    }
+    if (!active) continue;
+    D.H[(size_t)my * D.nkx + mx] = combine(SP, SM, nP, nM, D.norm, scale);
+  }
+}
+
+// V_s = sum_b w(b) |H_s(b)|^2 / N_R^2: partial sums (grid kVarBlocks x n_sets)
+__global__ void k_variance_partial_batched(const __grid_constant__ BatchParams B, double* part) {
+  __shared__ double red[256];
+  const SetDesc& D = B.s[blockIdx.y];
+  double sum = 0.0;
+  const int n = D.Ny * D.nkx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int mx = i % D.nkx;
+    const double w = (mx == 0 || 2 * mx == D.Nx) ? 1.0 : 2.0;
+    const float2 v = D.H[i];
+    sum += w * ((double)v.x * v.x + (double)v.y * v.y);
+  }
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_variance_final_batched(const __grid_constant__ BatchParams B,
+                                         const double* __restrict__ part, int nblk, double* var) {
+  __shared__ double red[128];
+  const int c = blockIdx.x;
+  double sum = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) sum += part[(size_t)c * nblk + b];
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double NR = (double)B.s[c].Ny * (double)B.s[c].Nx;
+  if (threadIdx.x == 0) var[c] = red[0] / (NR * NR);
+}
+
 // Fixed-order sum of per-block partials (deterministic).
 __global__ void k_reduce_partials(const double* partial, int nblk, int nv, double* out) {
   __shared__ double red[256];
@@ -539,5 +726,105 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   }
   if (phase_out && (e = launch_c2r_image(p, H, phase_out, nc, s)) != cudaSuccess) return e;
   stage_end(p, EER4D_STAGE_IMAGE, s);
+  return cudaSuccess;
+}
+
+namespace {
+struct BatchedLayout {
+  size_t coef, ek, gscale, vpart, H[kMaxSets], total;
+};
+BatchedLayout batched_layout(const eer4d_plan* const* plans, int n) {
+  BatchedLayout L;
+  const eer4d_plan* p0 = plans[0];
+  size_t o = 0;
+  L.coef = o; o = align256(o + sizeof(CandCoef) * n);
+  L.ek = o; o = align256(o + sizeof(float2) * (size_t)n * p0->P_pad);
+  L.gscale = o; o = align256(o + 2 * sizeof(double) * n);
+  L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    L.H[i] = o;
+    o = align256(o + sizeof(float2) * (size_t)plans[i]->g.scan_ny * plans[i]->nkx);
+  }
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t trotter_batched_scratch_bytes(const eer4d_plan* const* plans, int n) {
+  return batched_layout(plans, n).total;
+}
+
+cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2* const* G, int n,
+                                   const double* aberr, void* scratch, float* const* phase,
+                                   double* var, uint32_t* st, cudaStream_t s) {
+  const eer4d_plan* p0 = plans[0];
+  const BatchedLayout L = batched_layout(plans, n);
+  unsigned char* sb = static_cast<unsigned char*>(scratch);
+  CandCoef* coef = reinterpret_cast<CandCoef*>(sb + L.coef);
+  float2* ek = reinterpret_cast<float2*>(sb + L.ek);
+  double* gsc = reinterpret_cast<double*>(sb + L.gscale);
+  double* vpart = reinterpret_cast<double*>(sb + L.vpart);
+  BatchParams B;
+  B.n_sets = n;
+  B.P_pad = p0->P_pad;
+  B.P_bf = p0->P_bf;
+  B.k0sq = (float)(p0->g.k0_px * p0->g.k0_px);
+  int ntask = 0;
+  for (int i = 0; i < kMaxSets; ++i) {
+    SetDesc& D = B.s[i];
+    if (i >= n) {
+      D = B.s[0];
+      continue;
+    }
+    const eer4d_plan* p = plans[i];
+    D.G = G[i];
+    D.H = reinterpret_cast<float2*>(sb + L.H[i]);
+    D.Ny = p->g.scan_ny;
+    D.Nx = p->g.scan_nx;
+    D.nkx = p->nkx;
+    D.norm = p->norm;
+    D.kpm_x = (float)p->g.kpm_x;
+    D.kpm_y = (float)p->g.kpm_y;
+    D.task0 = ntask;
+    D.NR = (float)p->F;
+    ntask += p->nkx * ((D.Ny + 31) / 32);
+  }
+  B.ntask = ntask;
+  cudaError_t e;
+  stage_begin(p0, EER4D_STAGE_TROTTER, s);
+  k_prep<<<n, 256, 0, s>>>(aberr, n, p0->d_pix, p0->P_pad, p0->P, p0->g.dalpha_rad, p0->g.lambda_A,
+                           coef, ek, st, 1);
+  k_gbar_batched<<<n, 256, 0, s>>>(B, p0->d_bfp, gsc);
+  count_launches(2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t sm = sizeof(float2) * p0->P_bf + sizeof(int) * ((p0->P_bf + 1) & ~1);
+  const void* kern = (const void*)k_trotter_batched;
+  if ((e = ensure_smem(kern, sm)) != cudaSuccess) return e;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, sm);
+  int nblk = nsm * (occ > 0 ? occ : 1);
+  const int need = (ntask + kWarps - 1) / kWarps;
+  if (nblk > need) nblk = need;
+  if (nblk < 1) nblk = 1;
+  k_trotter_batched<<<nblk, kWarps * 32, sm, s>>>(B, p0->d_bfp, p0->d_pix, coef, ek, gsc);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  stage_end(p0, EER4D_STAGE_TROTTER, s);
+  stage_begin(p0, EER4D_STAGE_IMAGE, s);
+  if (var) {
+    k_variance_partial_batched<<<dim3(kVarBlocks, n), 256, 0, s>>>(B, vpart);
+    k_variance_final_batched<<<n, 128, 0, s>>>(B, vpart, kVarBlocks, var);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (phase) {
+    for (int i = 0; i < n; ++i) {
+      if (!phase[i]) continue;
+      if ((e = launch_c2r_image(plans[i], B.s[i].H, phase[i], 1, s)) != cudaSuccess) return e;
+    }
+  }
+  stage_end(p0, EER4D_STAGE_IMAGE, s);
   return cudaSuccess;
 }

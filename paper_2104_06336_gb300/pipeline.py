@@ -123,3 +123,21 @@ class Reconstructor:
         if code != L.EER4D_OK and raise_on_error:
             raise L.Eer4dError(code, "device status")
         return code
+
+
+def reconstruct_batched(recs, aberr: torch.Tensor, phase: bool = True, scratch=None):
+    """SSB phase images and variances of several datasets (one Reconstructor
+    each, same detector geometry, any scan sizes) in one trotter launch.
+    aberr: [n][5], row i for dataset i.  Returns (list of phases or None, var)."""
+    if not recs:
+        raise ValueError("no datasets")
+    dev = recs[0].device
+    ab = aberr.to(dev, torch.float64).reshape(len(recs), 5).contiguous()
+    plans = [r.plan for r in recs]
+    if scratch is None:
+        scratch = torch.empty(L.batched_scratch_bytes(plans), dtype=torch.uint8, device=dev)
+    ph = [torch.empty(r.Ny, r.Nx, dtype=torch.float32, device=dev) for r in recs] if phase else None
+    var = torch.empty(len(recs), dtype=torch.float64, device=dev)
+    L.ssb_reconstruct_batched(plans, [r.G for r in recs], ab, scratch, ph, var,
+                              status=recs[0].status)
+    return ph, var

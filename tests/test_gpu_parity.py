@@ -392,6 +392,85 @@ def test_full_size_workload_sampled_pixels_and_frequencies():
         assert np.abs(g - col).max() <= 2e-6 * scale, (ky, kx)
 
 
+# ------------------------------------------ uneven batches, one launch ------
+def _batch_cases(sizes, doses, seed=3):
+    out = []
+    for i, ((ny, nx), e) in enumerate(zip(sizes, doses)):
+        w = synth.workload(4, scan_ny=ny, scan_nx=nx, e_per_frame=float(e), seed=1000 * seed + i,
+                           name=f"batch{i}-{ny}x{nx}")
+        out.append(Case(w, device_gen="cuda"))
+    return out
+
+
+def test_batched_uneven_datasets_match_oracle_and_single():
+    """Datasets of the batching workload's detector (576x576 binned 4x, 1245
+    BF pixels) with different scan shapes and doses, each with its own
+    aberrations and scan rotation, in one ssb_reconstruct_batched call: every
+    phase within 1e-5 relative L2 of the FP64 oracle and equal to the
+    single-dataset path to 1e-6 of its max; variances within 1e-5."""
+    import paper_2104_06336_gb300 as P
+    cases = _batch_cases([(32, 32), (48, 64), (64, 48), (16, 16)], [10, 50, 30, 20])
+    ab = np.array([[60.0, 10.0, -20.0, 0.0, 0.0],
+                   [-40.0, 0.0, 15.0, 5.0e3, 0.0],
+                   [0.0, -25.0, 0.0, 0.0, 0.4],
+                   [120.0, 5.0, 5.0, 0.0, -0.2]])
+    ph, var = P.reconstruct_batched([c.rec for c in cases], torch.tensor(ab))
+    torch.cuda.synchronize()
+    assert cases[0].rec.check() == 0
+    for i, c in enumerate(cases):
+        phi, V = orc.ssb_phase(c.G_orc, c.geom, tuple(ab[i]), "none")
+        got = ph[i].cpu().numpy()
+        err = rel_l2(got, phi)
+        assert err <= 1e-5, (i, err)
+        assert abs(float(var[i]) - V) <= 1e-5 * V, (i, float(var[i]), V)
+        ph1, v1 = c.rec.reconstruct(torch.tensor(ab[i]))
+        d = np.abs(ph1[0].cpu().numpy() - got).max()
+        assert d <= 1e-6 * np.abs(got).max(), (i, d)
+
+
+def test_batched_rejects_mixed_detectors(c1):
+    """Datasets recorded with different detector geometries cannot share one
+    launch: the call returns EINVAL before enqueueing anything."""
+    import paper_2104_06336_gb300 as P
+    other = _batch_cases([(16, 16)], [10])[0]
+    with pytest.raises(P.Eer4dError) as ei:
+        P.reconstruct_batched([c1.rec, other.rec], torch.zeros(2, 5, dtype=torch.float64))
+    assert ei.value.code == -1
+
+
+def test_batching_workload_sixteen_datasets():
+    """The batching workload: 16 square scans N_i = 16 round(exp U(ln 64, ln 512)/16)
+    with 10..50 e-/frame, one launch.  Each dataset equals its single-dataset
+    reconstruction to 1e-6 of max|phi|; the smallest one against the oracle."""
+    import paper_2104_06336_gb300 as P
+    ws = synth.batching_datasets()
+    recs, small = [], None
+    for w in ws:
+        d = synth.generate(w, "cuda")
+        rec = P.Reconstructor(synth.geometry(w))
+        rec.load(d.idx, d.off)
+        recs.append(rec)
+        if small is None or w.scan_ny < small[0].scan_ny:
+            small = (w, d, rec)
+    torch.cuda.synchronize()
+    ab = torch.tensor(synth.candidate_aberrations(n=len(ws)))
+    ph, var = P.reconstruct_batched(recs, ab)
+    torch.cuda.synchronize()
+    assert recs[0].check() == 0
+    for i, rec in enumerate(recs):
+        ph1, v1 = rec.reconstruct(ab[i])
+        got = ph[i]
+        d = float((ph1[0] - got).abs().max())
+        assert d <= 1e-6 * float(got.abs().max()), (i, d)
+        assert abs(float(v1[0]) - float(var[i])) <= 1e-9 * float(var[i])
+    w, d, rec = small
+    i = recs.index(rec)
+    idx, off = d.numpy()
+    G = orc.g_function(orc.densify(idx, off, synth.geometry(w)), synth.geometry(w))
+    phi, V = orc.ssb_phase(G, synth.geometry(w), tuple(ab[i].numpy()), "none")
+    assert rel_l2(ph[i].cpu().numpy(), phi) <= 1e-5
+
+
 # ------------------------------------------ split-FP16 tensor-core DFT ------
 @pytest.mark.parametrize("which", ["c1", "c2small"])
 def test_split_fp16_dft_matches_fp32(which, request):
