@@ -139,6 +139,19 @@ int eer_load_csr(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx,
                  const uint64_t* d_off, uint64_t n_frames, int64_t* d_pacbed,
                  int64_t* d_totals, uint32_t* d_status, void* stream);
 
+/* ---- run-length-encoded EER (Sec. II, Fig. 1c; Table 1) ---------------------
+ * Re-codes run-length-encoded frames to linear-index encoding in O(C).  Within
+ * frame f (runs d_runs[d_off[f] .. d_off[f+1])) the hits are in ascending
+ * linear index and run j is the distance from the previous hit of the frame
+ * (run 0: the linear index of the first hit), so
+ *   d_idx[j] = run_0 + ... + run_j   (sums restart at every frame).
+ * d_idx (uint32 [n]) may be d_runs itself.  A sum above 2^32 - 1 is written as
+ * 0xFFFFFFFF (dropped as out of range by the other calls) and sets
+ * EER4D_ST_RANGE; offsets that decrease or pass n set EER4D_ST_OFFSETS (the
+ * frame's range is clipped).  Needs no plan. */
+int eer_decode_rle(const uint32_t* d_runs, uint64_t n, const uint64_t* d_off, uint64_t n_frames,
+                   uint32_t* d_idx, uint32_t* d_status, void* stream);
+
 /* ---- a2 + a3: centre of mass and DPC (Eq. 4; Sec. V) -----------------------
  * For the whole scan (n_frames = scan_ny*scan_nx): d_sums[3][F] (int64
  * Sx, Sy, N per frame, exact), d_com[2][F] (float, COM - centre in raw px; 0
@@ -150,6 +163,43 @@ int eer_load_csr(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx,
 int com_dpc(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
             int64_t* d_sums, float* d_com, float* d_phase, const int64_t* d_totals, double cx,
             double cy, double lam1, double lam2, void* d_scratch, uint32_t* d_status, void* stream);
+
+/* ---- virtual detectors (Table 1: operations in O(C) on linear-index EER) ----
+ * For every frame f the number of events in each of n_rings (1..EER4D_MAX_RINGS)
+ * annuli about the pattern centre: ring j holds the raw pixels (x, y) with
+ *   h_radii[j]^2 <= (x - cx)^2 + (y - cy)^2 < h_radii[j+1]^2
+ * (h_radii: host, n_rings + 1 ascending radii in raw px; squares and sums in
+ * double, round to nearest, no fused multiply-add).  One ring from 0 to the
+ * bright-field radius is a bright-field detector, an annulus outside it an
+ * annular dark-field one, many thin rings a radial sum.  The centre is
+ * d_totals[0..1]/d_totals[2] (the PACBED centre of mass from eer_load_csr)
+ * when d_totals is not NULL, else (cx, cy).  Output d_out int32
+ * [n_rings][n_frames] (ring-major, each ring an image in scan order).
+ * d_scratch needs det_w*det_h bytes (within eer4d_workspace_bytes' scratch).
+ * Events with idx >= det_w*det_h are dropped (EER4D_ST_RANGE), bad offsets
+ * set EER4D_ST_OFFSETS. */
+#define EER4D_MAX_RINGS 64
+int virtual_detectors(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx,
+                      const uint64_t* d_off, uint64_t n_frames, const double* h_radii, int n_rings,
+                      const int64_t* d_totals, double cx, double cy, void* d_scratch,
+                      int32_t* d_out, uint32_t* d_status, void* stream);
+
+/* ---- iterative regularised DPC (Sec. V) --------------------------------------
+ * The gradient-descent form of the DPC integration: with C = d_com (float
+ * [2][F], COM - centre in raw px as com_dpc writes it) times dalpha_raw/lambda,
+ *   R = M (C - grad phi^l / 2 pi),
+ *   phi^{l+1} = phi^l + mu IFFT[-i (Kx R^x + Ky R^y) / (lam1 + K^2 + lam2 K^4)],
+ * phi^0 = 0, n_iter steps (the update as printed has no residual; this is its
+ * reading), on a periodic grid of pad x pad times the scan (pad 1 or 2; with
+ * 2 the scan is the top-left quarter, M its indicator, so nothing wraps
+ * around).  Derivatives are spectral (iK); DC and Nyquist bins of the update
+ * are zero.  Output d_phase float [F] = phi^{n_iter} on the scan.  d_scratch
+ * needs 24 * pad^2 * F bytes (scratch_bytes is checked).  With pad = 1,
+ * lam1 = lam2 = 0 the result is (1 - (1 - mu)^n_iter) times com_dpc's
+ * one-shot integration on bins other than Nyquist. */
+int dpc_iterative(const eer4d_plan* plan, const float* d_com, double lam1, double lam2, double mu,
+                  int n_iter, int pad, void* d_scratch, size_t scratch_bytes, float* d_phase,
+                  void* stream);
 
 /* ---- a4 + a5: bin/crop/densify and the G function (Table 1; Sec. IV) -------
  * Scatters frames [first_frame, first_frame + n_frames) into the counts at
@@ -213,6 +263,17 @@ int ssb_trotter_counts(const eer4d_plan* plan, const double* d_aberr, int32_t* d
 int ssb_refocus_step(const eer4d_plan* plan, const void* d_G, double* d_aberr, const double* d_step,
                      void* d_scratch, float* d_phase, double* d_var, double* d_grad,
                      uint32_t* d_status, void* stream);
+
+/* ---- G-function viewer (Fig. 2, middle panel) -------------------------------
+ * G(k, K) at n (1..EER4D_MAX_SLICES) scan frequencies, for judging residual
+ * aberrations: h_bins (host) holds n pairs (m_y, m_x) of DFT bin indices
+ * (0 <= m_y < scan_ny, 0 <= m_x < scan_nx; bins with m_x > scan_nx/2 are read
+ * as conj G(k, -K)).  d_out complex64 [n][ph][pw] on the binned detector
+ * window: kept pixel k at (v, u) = (k_y + dc_v, k_x + dc_u), zero elsewhere.
+ * EINVAL for a bin out of range. */
+#define EER4D_MAX_SLICES 64
+int ssb_g_slices(const eer4d_plan* plan, const void* d_G, const int32_t* h_bins, int n,
+                 void* d_out, void* stream);
 
 /* ---- several datasets in one launch (Sec. IV, S(K) of Eq. 3 per dataset) -----
  * Uneven batches: n_sets (1..EER4D_MAX_SETS) datasets recorded with one

@@ -42,7 +42,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "pixel_table", "frame_of_events", "event_pixels", "densify", "densify_pixels", "g_column",
+    "rle_decode", "rle_decode_fast", "virtual_detector_counts", "dpc_iterative", "pixel_table", "frame_of_events", "event_pixels", "densify", "densify_pixels", "g_column", "g_slices",
     "bin_crop_dense", "com_sums", "com_sums_dense",
     "pacbed", "pacbed_centre", "com_maps", "idpc", "g_function", "gbar0", "chi_turns",
     "kprime_f32", "kprime_f64", "trotter_mask", "ssb_spectrum", "ssb_phase", "ssb_grad",
@@ -157,6 +157,34 @@ def bin_crop_dense(cube: np.ndarray, geom) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Run-length encoding (Sec. II, Fig. 1c: only the distance between hits is kept)
+# --------------------------------------------------------------------------
+def rle_decode(runs, off) -> np.ndarray:
+    """Linear indices from run-length-encoded frames: within each frame the
+    index of hit j is the sum of runs 0..j (the first run counts from pixel
+    0).  Python-int sums per frame; returned as int64."""
+    runs = np.asarray(runs, dtype=np.int64)
+    off = np.asarray(off, dtype=np.int64)
+    out = np.empty_like(runs)
+    for f in range(len(off) - 1):
+        acc = 0
+        for j in range(int(off[f]), int(off[f + 1])):
+            acc += int(runs[j])
+            out[j] = acc
+    return out
+
+
+def rle_decode_fast(runs, off) -> np.ndarray:
+    """The same sums as rle_decode for large inputs: one cumulative sum minus
+    the running total at each frame start."""
+    runs = np.asarray(runs, dtype=np.int64)
+    off = np.asarray(off, dtype=np.int64)
+    c = np.cumsum(runs)
+    before = np.concatenate(([0], c))[off[:-1]]
+    return c - np.repeat(before, np.diff(off))
+
+
+# --------------------------------------------------------------------------
 # Centre of mass (Eq. 4; Table 1 "center of mass"; Sec. V)
 # --------------------------------------------------------------------------
 def com_sums(idx, off, det_w, det_h):
@@ -188,6 +216,26 @@ def com_sums_dense(cube: np.ndarray):
     ys = np.arange(H, dtype=dt)
     return ((c * xs[None, None, :]).sum(axis=(1, 2)), (c * ys[None, :, None]).sum(axis=(1, 2)),
             c.sum(axis=(1, 2)))
+
+
+def virtual_detector_counts(idx, off, det_w, det_h, radii, cx, cy) -> np.ndarray:
+    """Virtual annular detectors (Table 1, O(C) on linear-index EER): counts
+    [n_rings][F], ring j = raw pixels with radii[j]^2 <= (x-cx)^2 + (y-cy)^2
+    < radii[j+1]^2 (float64 squares and sums, one rounding each)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    F = len(off) - 1
+    f = frame_of_events(off)
+    ok = idx < det_w * det_h
+    x, y = _xy(idx[ok], det_w)
+    dx = x.astype(np.float64) - cx
+    dy = y.astype(np.float64) - cy
+    r2 = dx * dx + dy * dy
+    edges = np.array([float(r) * float(r) for r in radii])
+    ring = np.searchsorted(edges, r2, side="right") - 1
+    keep = (ring >= 0) & (ring < len(radii) - 1)
+    n_rings = len(radii) - 1
+    flat = np.bincount(ring[keep] * F + f[ok][keep], minlength=n_rings * F)
+    return flat.reshape(n_rings, F).astype(np.int64)
 
 
 def pacbed(idx, det_w, det_h) -> np.ndarray:
@@ -238,6 +286,48 @@ def idpc(comx, comy, geom, lam1=0.0, lam2=0.0) -> np.ndarray:
     return np.fft.ifft2(Phi).real
 
 
+def dpc_iterative(comx, comy, geom, n_iter, mu=0.5, lam1=0.0, lam2=0.0, pad=2) -> np.ndarray:
+    """The gradient-descent DPC of Sec. V, step by step.  The printed update
+    has no residual term; it is read as
+      R = M (C - grad(phi^l) / 2 pi),
+      phi^{l+1} = phi^l + mu IFFT[-i (Kx FFT(Rx) + Ky FFT(Ry)) / (lam1 + K^2 + lam2 K^4)],
+    phi^0 = 0, on a periodic grid of pad x the scan with the scan in the
+    top-left corner and M its indicator.  Gradients are spectral (FFT, times
+    i K, inverse FFT); the DC and Nyquist bins of the update and of the
+    derivative are zero.  Returns phi^{n_iter} on the scan."""
+    Ny, Nx = geom["scan_ny"], geom["scan_nx"]
+    My, Mx = pad * Ny, pad * Nx
+    s = geom["dalpha_raw_rad"] / geom["lambda_A"]
+    Cx = np.zeros((My, Mx))
+    Cy = np.zeros((My, Mx))
+    Cx[:Ny, :Nx] = np.asarray(comx, dtype=np.float64).reshape(Ny, Nx) * s
+    Cy[:Ny, :Nx] = np.asarray(comy, dtype=np.float64).reshape(Ny, Nx) * s
+    M = np.zeros((My, Mx))
+    M[:Ny, :Nx] = 1.0
+    Kx = np.fft.fftfreq(Mx, d=geom["step_A"])[None, :]
+    Ky = np.fft.fftfreq(My, d=geom["step_A"])[:, None]
+    K2 = Kx * Kx + Ky * Ky
+    den = lam1 + K2 + lam2 * K2 * K2
+    zero = np.zeros((My, Mx), dtype=bool)
+    zero[:, Mx // 2] = True
+    zero[My // 2, :] = True
+    upd_zero = zero | (den == 0)
+    upd_zero[0, 0] = True
+    phi = np.zeros((My, Mx))
+    for _ in range(n_iter):
+        P = np.fft.fft2(phi)
+        P[zero] = 0.0
+        gx = np.fft.ifft2(1j * Kx * P).real
+        gy = np.fft.ifft2(1j * Ky * P).real
+        Rx = M * (Cx - gx)
+        Ry = M * (Cy - gy)
+        num = -1j * (Kx * np.fft.fft2(Rx) + Ky * np.fft.fft2(Ry))
+        U = np.zeros((My, Mx), dtype=np.complex128)
+        U[~upd_zero] = num[~upd_zero] / den[~upd_zero]
+        phi = phi + mu * np.fft.ifft2(U).real
+    return phi[:Ny, :Nx]
+
+
 # --------------------------------------------------------------------------
 # G function (Sec. IV: G(k, K) = F_{R->K} I(k, R))
 # --------------------------------------------------------------------------
@@ -262,6 +352,17 @@ def g_column(idx, off, geom, ky, kx) -> np.ndarray:
     re = np.bincount(p[keep], weights=np.cos(ph), minlength=P)
     im = np.bincount(p[keep], weights=np.sin(ph), minlength=P)
     return re + 1j * im
+
+
+def g_slices(G, geom, bins) -> np.ndarray:
+    """G(k, K) at the DFT bins (m_y, m_x) laid out on the binned detector
+    window [n][ph][pw] (zero outside the kept pixels), the G-function view of
+    Fig. 2.  G is the full [P][Ny][Nx] array of g_function."""
+    pt = pixel_table(geom)
+    out = np.zeros((len(bins), geom["ph"], geom["pw"]), dtype=np.complex128)
+    for s, (my, mx) in enumerate(bins):
+        out[s, pt["v"], pt["u"]] = G[:, my, mx]
+    return out
 
 
 def gbar0(G, geom) -> float:

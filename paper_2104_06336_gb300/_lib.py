@@ -28,8 +28,11 @@ EXPORTS = [
     "eer4d_status_code", "eer4d_strerror", "eer4d_last_error", "eer_load_csr", "com_dpc",
     "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
-    "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched",
+    "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
+    "virtual_detectors", "ssb_g_slices", "dpc_iterative",
 ]
+MAX_SLICES = 64
+MAX_RINGS = 64
 MAX_SETS = 32
 STAGES = ["validate", "com", "dpc", "scatter", "dft_x", "dft_y", "trotter", "image", "dft_xy"]
 
@@ -96,6 +99,10 @@ def load(path: str | None = None):
         "ssb_reconstruct_static": (I32, [P, P, P, P, P, P, P]),
         "eer4d_batched_scratch_bytes": (I32, [P, I32, C.POINTER(S)]),
         "ssb_reconstruct_batched": (I32, [P, P, I32, P, P, P, P, P, P]),
+        "eer_decode_rle": (I32, [P, U64, P, U64, P, P, P]),
+        "dpc_iterative": (I32, [P, P, D, D, D, I32, I32, P, S, P, P]),
+        "ssb_g_slices": (I32, [P, P, C.POINTER(C.c_int32), I32, P, P]),
+        "virtual_detectors": (I32, [P, P, U64, P, U64, C.POINTER(D), I32, P, D, D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -276,3 +283,46 @@ def ssb_reconstruct_batched(plans, Gs, aberr, scratch, phases=None, var=None, st
                                           _ptr(scratch, "scratch"), ph_arr, _ptr(var, "var"),
                                           _ptr(status, "status"), _stream()),
            "ssb_reconstruct_batched")
+
+
+def eer_decode_rle(runs, off, idx=None, status=None):
+    """Run-length-encoded frames (uint32 runs, uint64 CSR offsets) to linear
+    indices; returns idx (a new int32 tensor of uint32 values unless given;
+    ``idx=runs`` decodes in place)."""
+    if idx is None:
+        idx = torch.empty_like(runs)
+    _check(load().eer_decode_rle(_ptr(runs, "runs"), runs.numel(), _ptr(off, "off"),
+                                 off.numel() - 1, _ptr(idx, "idx"), _ptr(status, "status"),
+                                 _stream()), "eer_decode_rle")
+    return idx
+
+
+def virtual_detectors(plan: Plan, idx, off, radii, out, scratch, totals=None, cx=0.0, cy=0.0,
+                      status=None):
+    """Per-frame event counts in the annuli radii[j] <= r < radii[j+1] (raw px)
+    about the PACBED centre (totals) or (cx, cy); out int32 [n_rings][F]."""
+    r = [float(x) for x in radii]
+    arr = (C.c_double * len(r))(*r)
+    _check(load().virtual_detectors(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                                    off.numel() - 1, arr, len(r) - 1, _ptr(totals, "totals"),
+                                    float(cx), float(cy), _ptr(scratch, "scratch"),
+                                    _ptr(out, "out"), _ptr(status, "status"), _stream()),
+           "virtual_detectors")
+
+
+def ssb_g_slices(plan: Plan, G, bins, out):
+    """G(k, K) at the DFT bins [(m_y, m_x), ...] on the binned detector window:
+    out complex64 [n][ph][pw] (as a float32 [n][ph][pw][2] or complex tensor)."""
+    flat = [int(v) for b in bins for v in b]
+    arr = (C.c_int32 * len(flat))(*flat)
+    _check(load().ssb_g_slices(plan.handle, _ptr(G, "G"), arr, len(bins), _ptr(out, "out"),
+                               _stream()), "ssb_g_slices")
+
+
+def dpc_iterative(plan: Plan, com, phase, scratch, n_iter: int, mu: float = 0.5, lam1: float = 0.0,
+                  lam2: float = 0.0, pad: int = 2):
+    """Iterative regularised DPC from COM maps (float32 [2][F], raw px)."""
+    _check(load().dpc_iterative(plan.handle, _ptr(com, "com"), float(lam1), float(lam2), float(mu),
+                                int(n_iter), int(pad), _ptr(scratch, "scratch"),
+                                scratch.numel() * scratch.element_size(), _ptr(phase, "phase"),
+                                _stream()), "dpc_iterative")

@@ -90,6 +90,8 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_rows);
   cudaFree(p->d_tw_y);
   cudaFree(p->d_tw_x);
+  cudaFree(p->d_tw_y2);
+  cudaFree(p->d_tw_x2);
   cudaFree(p->d_dft_hi);
   cudaFree(p->d_dft_lo);
   free(p);
@@ -220,7 +222,9 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
       (e = upload(&p->d_bfp, bfp)) != cudaSuccess ||
       (e = upload(&p->d_rows, rows)) != cudaSuccess ||
       (e = make_fft((int)g.scan_ny, p->fy, &p->d_tw_y)) != cudaSuccess ||
-      (e = make_fft((int)g.scan_nx, p->fx, &p->d_tw_x)) != cudaSuccess) {
+      (e = make_fft((int)g.scan_nx, p->fx, &p->d_tw_x)) != cudaSuccess ||
+      (e = make_fft(2 * (int)g.scan_ny, p->fy2, &p->d_tw_y2)) != cudaSuccess ||
+      (e = make_fft(2 * (int)g.scan_nx, p->fx2, &p->d_tw_x2)) != cudaSuccess) {
     const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
     free_plan(p);
     return rc;
@@ -255,6 +259,7 @@ int eer4d_workspace_bytes(const eer4d_plan* p, int n_cand, size_t* counts_bytes,
   if (G_bytes) *G_bytes = sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
   if (scratch_bytes) {
     size_t s = sizeof(float2) * (size_t)p->F;  // com_dpc
+    if (vdet_scratch_bytes(p) > s) s = vdet_scratch_bytes(p);
     size_t r = trotter_scratch_bytes(p, n_cand, TROT_FWD);
     if (r > s) s = r;
     r = trotter_scratch_bytes(p, 1, TROT_GRAD) + sizeof(float2) * (size_t)p->g.scan_ny * p->nkx;
@@ -300,6 +305,37 @@ int eer_load_csr(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, con
   if (n_frames == 0) return EER4D_OK;
   return cuda_fail(launch_validate(p, d_idx, n_idx, d_off, n_frames, d_pacbed, d_totals, d_status,
                                    (cudaStream_t)stream));
+}
+
+int eer_decode_rle(const uint32_t* d_runs, uint64_t n, const uint64_t* d_off, uint64_t n_frames,
+                   uint32_t* d_idx, uint32_t* d_status, void* stream) {
+  if (!d_off || (n && (!d_runs || !d_idx))) return EER4D_EINVAL;
+  return cuda_fail(launch_rle_decode(d_runs, n, d_off, n_frames, d_idx, d_status,
+                                     (cudaStream_t)stream));
+}
+
+int virtual_detectors(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx,
+                      const uint64_t* d_off, uint64_t n_frames, const double* h_radii, int n_rings,
+                      const int64_t* d_totals, double cx, double cy, void* d_scratch,
+                      int32_t* d_out, uint32_t* d_status, void* stream) {
+  if (!p || !d_off || (n_idx && !d_idx) || !h_radii || !d_scratch || !d_out) return EER4D_EINVAL;
+  if (n_rings < 1 || n_rings > EER4D_MAX_RINGS) return EER4D_EINVAL;
+  for (int j = 0; j <= n_rings; ++j)
+    if (!(h_radii[j] >= 0.0) || (j && h_radii[j] < h_radii[j - 1])) return EER4D_EINVAL;
+  return cuda_fail(launch_virtual_detectors(p, d_idx, n_idx, d_off, n_frames, h_radii, n_rings,
+                                            d_totals, cx, cy, d_scratch, d_out, d_status,
+                                            (cudaStream_t)stream));
+}
+
+int dpc_iterative(const eer4d_plan* p, const float* d_com, double lam1, double lam2, double mu,
+                  int n_iter, int pad, void* d_scratch, size_t scratch_bytes, float* d_phase,
+                  void* stream) {
+  if (!p || !d_com || !d_scratch || !d_phase) return EER4D_EINVAL;
+  if ((pad != 1 && pad != 2) || n_iter < 0 || n_iter > 100000) return EER4D_EINVAL;
+  if (!(mu > 0.0 && mu < 2.0) || !(lam1 >= 0.0) || !(lam2 >= 0.0)) return EER4D_EINVAL;
+  if (scratch_bytes < dpc_iterative_scratch_bytes(p, pad)) return EER4D_EINVAL;
+  return cuda_fail(launch_dpc_iterative(p, d_com, lam1, lam2, mu, n_iter, pad, d_scratch, d_phase,
+                                        (cudaStream_t)stream));
 }
 
 int com_dpc(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
@@ -435,6 +471,17 @@ int ssb_reconstruct_batched(const eer4d_plan* const* plans, const void* const* d
   }
   return cuda_fail(launch_trotter_batched(plans, G, n, d_aberr, d_scratch, d_phase, d_var,
                                           d_status, (cudaStream_t)stream));
+}
+
+int ssb_g_slices(const eer4d_plan* p, const void* d_G, const int32_t* h_bins, int n, void* d_out,
+                 void* stream) {
+  if (!p || !d_G || !h_bins || !d_out || n < 1 || n > EER4D_MAX_SLICES) return EER4D_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (h_bins[2 * i] < 0 || h_bins[2 * i] >= (int)p->g.scan_ny || h_bins[2 * i + 1] < 0 ||
+        h_bins[2 * i + 1] >= (int)p->g.scan_nx)
+      return EER4D_EINVAL;
+  return cuda_fail(launch_g_slices(p, static_cast<const float2*>(d_G), h_bins, n,
+                                   static_cast<float2*>(d_out), (cudaStream_t)stream));
 }
 
 int ssb_trotter_counts(const eer4d_plan* p, const double* d_aberr, int32_t* d_count,

@@ -67,7 +67,9 @@ struct eer4d_plan {
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
   float2* d_tw_y;            // [scan_ny]
   float2* d_tw_x;            // [scan_nx]
-  FftDesc fy, fx;
+  float2* d_tw_y2;           // [2 scan_ny] (zero-padded DPC grid)
+  float2* d_tw_x2;           // [2 scan_nx]
+  FftDesc fy, fx, fy2, fx2;
   // streaming state of ssb_accumulate (host)
   uint64_t next_frame;
   // optional per-stage timing events (caller-owned cudaEvent_t), see
@@ -127,6 +129,15 @@ cudaError_t launch_validate(const eer4d_plan* p, const uint32_t* idx, uint64_t n
 cudaError_t launch_com(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx, const uint64_t* off,
                        int64_t* sums, float* com, float2* z, const int64_t* totals, double cx,
                        double cy, uint32_t* st, cudaStream_t s);
+cudaError_t launch_g_slices(const eer4d_plan* p, const float2* G, const int32_t* bins, int n,
+                            float2* out, cudaStream_t s);
+size_t vdet_scratch_bytes(const eer4d_plan* p);
+cudaError_t launch_virtual_detectors(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
+                                     const uint64_t* off, uint64_t n_frames, const double* radii,
+                                     int n_rings, const int64_t* totals, double cx, double cy,
+                                     void* scratch, int32_t* out, uint32_t* st, cudaStream_t s);
+cudaError_t launch_rle_decode(const uint32_t* runs, uint64_t n, const uint64_t* off,
+                              uint64_t n_frames, uint32_t* idx, uint32_t* st, cudaStream_t s);
 cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                            const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
                            uint32_t* st, cudaStream_t s);
@@ -151,6 +162,13 @@ cudaError_t launch_dft2_fused(const eer4d_plan* p, const __half* counts, float2*
                               unsigned* ctl, uint32_t* st, cudaStream_t s);
 cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam1, double lam2,
                         cudaStream_t s);
+// complex 2D transform in place over [fy.N][fx.N], output scaled by scale
+cudaError_t launch_fft2_c2c(const FftDesc& fy, const FftDesc& fx, float2* data, int dir,
+                            float scale, cudaStream_t s);
+size_t dpc_iterative_scratch_bytes(const eer4d_plan* p, int pad);
+cudaError_t launch_dpc_iterative(const eer4d_plan* p, const float* com, double lam1, double lam2,
+                                 double mu, int n_iter, int pad, void* scratch, float* phase,
+                                 cudaStream_t s);
 cudaError_t launch_c2r_image(const eer4d_plan* p, float2* H, float* phase, int n_cand, cudaStream_t s);
 cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cudaStream_t s);
 

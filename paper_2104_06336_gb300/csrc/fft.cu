@@ -389,6 +389,19 @@ cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cud
   return cols(p->fy, W, W, 1, nkx, nkx, nkx, bs, bs, 1, 1.f, s);
 }
 
+cudaError_t launch_fft2_c2c(const FftDesc& fy, const FftDesc& fx, float2* data, int dir,
+                            float scale, cudaStream_t s) {
+  const int My = fy.N, Mx = fx.N;
+  const int nb = rows_nb(Mx);
+  const size_t sm = (size_t)2 * nb * Mx * sizeof(float2);
+  cudaError_t e = set_smem(k_rows_c2c, sm);
+  if (e != cudaSuccess) return e;
+  k_rows_c2c<<<(My + nb - 1) / nb, kThreads, sm, s>>>(data, nullptr, fx, My, nb, dir, 1.f);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cols(fy, data, data, dir, Mx, Mx, Mx, 0, 0, 1, scale, s);
+}
+
 cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam1, double lam2,
                         cudaStream_t s) {
   const int Ny = p->g.scan_ny, Nx = p->g.scan_nx;

@@ -78,6 +78,25 @@ class Reconstructor:
                   scratch=self.scratch, status=self.status)
         return sums, com, ph
 
+    def dpc_iterative(self, com: torch.Tensor, n_iter: int, mu: float = 0.5, lam1: float = 0.0,
+                      lam2: float = 0.0, pad: int = 2) -> torch.Tensor:
+        """Iterative regularised DPC phase [Ny][Nx] from COM maps [2][F]."""
+        scr = torch.empty(24 * pad * pad * self.F, dtype=torch.uint8, device=self.device)
+        ph = torch.empty(self.Ny, self.Nx, dtype=torch.float32, device=self.device)
+        L.dpc_iterative(self.plan, com.to(torch.float32).contiguous(), ph, scr, n_iter, mu=mu,
+                        lam1=lam1, lam2=lam2, pad=pad)
+        return ph
+
+    def virtual_detectors(self, idx: torch.Tensor, off: torch.Tensor, radii, use_totals=True,
+                          cx=0.0, cy=0.0) -> torch.Tensor:
+        """Per-frame event counts in annuli radii[j] <= r < radii[j+1] (raw px)
+        about the PACBED centre: int32 [n_rings][Ny][Nx] images."""
+        out = torch.empty(len(radii) - 1, self.F, dtype=torch.int32, device=self.device)
+        L.virtual_detectors(self.plan, as_u32(idx), off.contiguous(), radii, out, self.scratch,
+                            totals=self.totals if use_totals else None, cx=cx, cy=cy,
+                            status=self.status)
+        return out.view(-1, self.Ny, self.Nx)
+
     # -- SSB -----------------------------------------------------------------
     def reconstruct(self, aberr: torch.Tensor, phase: bool = True):
         """SSB phase images and variances for aberration candidates [n][5]."""
@@ -111,6 +130,14 @@ class Reconstructor:
         cnt = torch.empty(self.Ny, self.Nx, dtype=torch.int32, device=self.device)
         L.ssb_trotter_counts(self.plan, ab, cnt, self.scratch)
         return cnt
+
+    def g_slices(self, bins) -> torch.Tensor:
+        """G(k, K) at DFT bins [(m_y, m_x), ...] on the binned detector window:
+        complex64 [n][ph][pw] (zero outside the crop)."""
+        out = torch.empty(len(bins), self.geom["ph"], self.geom["pw"], dtype=torch.complex64,
+                          device=self.device)
+        L.ssb_g_slices(self.plan, self.G, bins, out)
+        return out
 
     # -- views -----------------------------------------------------------------
     def G_complex(self) -> torch.Tensor:

@@ -37,6 +37,25 @@ class EventData:
     def n_events(self) -> int:
         return int(self.idx.numel())
 
+    def rle(self):
+        """The same frames in run-length encoding (the format of detectors that
+        store the distance between hits, Fig. 1c): hits sorted by linear index
+        within each frame, each run the distance from the previous hit (the
+        first run from pixel 0).  Returns (runs, off) on the events' device."""
+        idx = self.idx.to(torch.int64) & 0xFFFFFFFF
+        F = self.off.numel() - 1
+        frame = torch.repeat_interleave(torch.arange(F, device=idx.device),
+                                        self.off[1:] - self.off[:-1])
+        key = frame * (1 << 32) + idx
+        srt = torch.sort(key).values & 0xFFFFFFFF
+        prev = torch.zeros_like(srt)
+        prev[1:] = srt[:-1]
+        first = torch.zeros_like(srt, dtype=torch.bool)
+        starts = self.off[:-1][self.off[:-1] < self.off[1:]]
+        first[starts] = True
+        runs = torch.where(first, srt, srt - prev)
+        return runs.to(torch.int32), self.off.clone()
+
     def numpy(self):
         """(idx uint32, off uint64) numpy views for the oracle."""
         idx = self.idx.cpu().numpy().view(np.uint32)

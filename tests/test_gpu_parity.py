@@ -392,6 +392,107 @@ def test_full_size_workload_sampled_pixels_and_frequencies():
         assert np.abs(g - col).max() <= 2e-6 * scale, (ky, kx)
 
 
+# ------------------------------------------------------- iterative DPC ------
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+@pytest.mark.parametrize("pad,n_iter,lam1", [(2, 50, 0.0), (1, 7, 0.3), (2, 0, 0.0)])
+def test_dpc_iterative_matches_oracle(which, pad, n_iter, lam1, request):
+    """The gradient-descent DPC (mu = 0.5) from the oracle's COM maps, within
+    1e-5 relative L2 of the FP64 iteration (zero steps: exactly zero)."""
+    c = request.getfixturevalue(which)
+    W, H = c.w.det_w, c.w.det_h
+    Sx, Sy, N = orc.com_sums(c.idx_np, c.off_np, W, H)
+    cx, cy = orc.pacbed_centre(Sx, Sy, N)
+    ox, oy = orc.com_maps(Sx, Sy, N, cx, cy)
+    com = torch.tensor(np.stack([ox, oy]).astype(np.float32), device="cuda")
+    ph = c.rec.dpc_iterative(com, n_iter, mu=0.5, lam1=lam1, pad=pad).cpu().numpy()
+    ref = orc.dpc_iterative(com.cpu().numpy()[0].astype(np.float64), com.cpu().numpy()[1].astype(np.float64),
+                            c.geom, n_iter, mu=0.5, lam1=lam1, pad=pad)
+    if n_iter == 0:
+        assert np.all(ph == 0)
+    else:
+        assert rel_l2(ph, ref) <= 1e-5, rel_l2(ph, ref)
+
+
+# ---------------------------------------------------- G-function view ------
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_g_slices_match_oracle(which, request):
+    """G(k, K) at nine bins, including bins of the unstored K_x < 0 half
+    (conjugate symmetry) and Nyquist bins, on the detector window."""
+    c = request.getfixturevalue(which)
+    Ny, Nx = c.w.scan_ny, c.w.scan_nx
+    bins = [(0, 0), (1, 0), (0, 1), (3, 5), (Ny - 3, Nx - 5), (Ny // 2, 0), (0, Nx // 2),
+            (Ny - 1, 2), (7, Nx - 1)]
+    got = c.rec.g_slices(bins).cpu().numpy()
+    ref = orc.g_slices(c.G_orc, c.geom, bins)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(c.G_orc).max()
+    assert np.all(got[ref == 0] == 0)
+
+
+# ------------------------------------------------- virtual detectors ------
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_virtual_detectors_bit_exact(which, request):
+    """Bright-field disk, annular and dark-field rings and a 16-ring radial sum
+    about the PACBED centre, bit-exact against the oracle."""
+    c = request.getfixturevalue(which)
+    W, H = c.w.det_w, c.w.det_h
+    Sx, Sy, N = orc.com_sums(c.idx_np, c.off_np, W, H)
+    cx, cy = orc.pacbed_centre(Sx, Sy, N)
+    bf = c.geom["k0_px"] * c.geom["bin"]
+    for radii in ([0.0, bf], [0.0, 0.5 * bf, bf, 2 * bf, 4.0 * max(W, H)],
+                  list(np.linspace(0.0, 1.5 * bf, 17))):
+        got = c.rec.virtual_detectors(c.idx, c.off, radii).cpu().numpy().reshape(len(radii) - 1, -1)
+        ref = orc.virtual_detector_counts(c.idx_np, c.off_np, W, H, radii, cx, cy)
+        np.testing.assert_array_equal(got, ref)
+    assert c.rec.check() == 0
+
+
+# ------------------------------------------- run-length-encoded ingest -----
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_rle_decode_bit_exact_and_pipeline(which, request):
+    """eer_decode_rle against the oracle's prefix sums, bit for bit; the decoded
+    (per-frame sorted) events give the same COM sums and G as the original
+    linear-index events; decoding in place gives the same indices."""
+    import paper_2104_06336_gb300 as P
+    c = request.getfixturevalue(which)
+    ev = synth.EventData(idx=c.idx, off=c.off, phi_scan=torch.zeros(1))
+    runs, off = ev.rle()
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    idx = P.eer_decode_rle(runs, off, status=st)
+    torch.cuda.synchronize()
+    assert P.status_code(st) == 0
+    ref = orc.rle_decode_fast(runs.cpu().numpy().view(np.uint32), off.cpu().numpy())
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32).astype(np.int64), ref)
+    inplace = runs.clone()
+    P.eer_decode_rle(inplace, off, idx=inplace, status=st)
+    assert torch.equal(inplace, idx)
+    rec = P.Reconstructor(c.geom)
+    rec.load(idx, off)
+    sums, _, _ = rec.com_dpc(idx, off)
+    sums0, _, _ = c.rec.com_dpc(c.idx, c.off)
+    torch.cuda.synchronize()
+    assert torch.equal(sums, sums0)
+    assert torch.equal(rec.counts, c.rec.counts)
+    assert torch.equal(rec.G, c.rec.G)
+
+
+def test_rle_decode_flags_overflow_and_bad_offsets():
+    """A frame whose runs add up past 2^32 - 1 is written as 0xFFFFFFFF and
+    flagged as out of range; decreasing offsets are flagged and clipped."""
+    import paper_2104_06336_gb300 as P
+    runs = torch.tensor([5, 10, -1, 3], dtype=torch.int32, device="cuda")  # -1 = 0xFFFFFFFF
+    off = torch.tensor([0, 2, 4], dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    idx = P.eer_decode_rle(runs, off, status=st)
+    torch.cuda.synchronize()
+    assert idx.cpu().numpy().view(np.uint32).tolist() == [5, 15, 0xFFFFFFFF, 0xFFFFFFFF]
+    assert P.status_code(st) == P._lib.EER4D_ERANGE
+    st.zero_()
+    bad = torch.tensor([0, 3, 1], dtype=torch.int64, device="cuda")
+    P.eer_decode_rle(runs, bad, status=st)
+    torch.cuda.synchronize()
+    assert P.status_code(st) == P._lib.EER4D_EOFFSETS
+
+
 # ------------------------------------------ uneven batches, one launch ------
 def _batch_cases(sizes, doses, seed=3):
     out = []

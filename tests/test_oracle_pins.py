@@ -127,6 +127,79 @@ def test_g_column_equals_brute_force_sum():
         assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
 
 
+def test_rle_decode_golden_frames():
+    """Hand-worked frames of run-length encoding (Fig. 1c), including an
+    empty frame, a hit at pixel 0, a repeated hit and a hit at the last pixel
+    of a 576x576 detector."""
+    g = json.load(open(os.path.join(GOLDEN, "rle_frames.json")))
+    runs = [r for fr in g["frames"] for r in fr["runs"]]
+    off = np.cumsum([0] + [len(fr["runs"]) for fr in g["frames"]])
+    hits = [h for fr in g["frames"] for h in fr["hits"]]
+    assert orc.rle_decode(runs, off).tolist() == hits
+    assert orc.rle_decode_fast(runs, off).tolist() == hits
+
+
+def test_rle_round_trip_of_generated_frames():
+    """Decoding the generator's run-length form returns each frame's hits in
+    ascending order (the multiset of the linear-index frame)."""
+    w = synth.workload(1)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    runs, roff = d.rle()
+    dec = orc.rle_decode_fast(runs.numpy().view(np.uint32), roff.numpy())
+    o = off.astype(np.int64)
+    for f in range(len(o) - 1):
+        np.testing.assert_array_equal(dec[o[f]:o[f + 1]], np.sort(idx[o[f]:o[f + 1]].astype(np.int64)))
+    small = slice(0, int(o[40]))
+    np.testing.assert_array_equal(orc.rle_decode(runs.numpy()[small].view(np.uint32), roff.numpy()[:41]),
+                                  dec[small])
+
+
+def test_virtual_detectors_equal_dense_masks():
+    """Annular virtual detectors from events equal the dense-format sums over
+    boolean ring masks built pixel by pixel with Python floats; rings that
+    cover the whole detector add up to the frame's event count."""
+    w = synth.workload(1)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    cube = _dense_cube(idx, off, w.det_w, w.det_h)
+    Sx, Sy, N = orc.com_sums(idx, off, w.det_w, w.det_h)
+    cx, cy = orc.pacbed_centre(Sx, Sy, N)
+    radii = [0.0, 5.0, 12.5, 20.0, 31.0, 100.0]
+    got = orc.virtual_detector_counts(idx, off, w.det_w, w.det_h, radii, cx, cy)
+    ring = np.full((w.det_h, w.det_w), -1)
+    for yy in range(w.det_h):
+        for xx in range(w.det_w):
+            r2 = (xx - cx) * (xx - cx) + (yy - cy) * (yy - cy)
+            for j in range(len(radii) - 1):
+                if radii[j] * radii[j] <= r2 < radii[j + 1] * radii[j + 1]:
+                    ring[yy, xx] = j
+    for j in range(len(radii) - 1):
+        np.testing.assert_array_equal(got[j], cube[:, ring == j].sum(axis=1))
+    np.testing.assert_array_equal(got.sum(axis=0), N)  # 100 px covers the 64x64 detector
+
+
+def test_g_slices_place_event_sums_on_the_detector():
+    """The G-function view at nine bins (DC, positive, negative, Nyquist) equals
+    the event-sum DFT of each kept pixel written at its detector position."""
+    w = synth.workload(1)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    geom = synth.geometry(w)
+    G = orc.g_function(orc.densify(idx, off, geom), geom)
+    Ny, Nx = w.scan_ny, w.scan_nx
+    bins = [(0, 0), (1, 0), (0, 1), (3, 5), (Ny - 3, Nx - 5), (Ny // 2, 0), (0, Nx // 2),
+            (Ny - 1, 2), (7, Nx - 1)]
+    got = orc.g_slices(G, geom, bins)
+    pt = orc.pixel_table(geom)
+    for s, (my, mx) in enumerate(bins):
+        col = orc.g_column(idx, off, geom, my, mx)
+        ref = np.zeros((geom["ph"], geom["pw"]), dtype=np.complex128)
+        for p in range(pt["P"]):
+            ref[pt["v"][p], pt["u"][p]] = col[p]
+        assert np.abs(got[s] - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+
+
 # ------------------------------------------------------------------- COM ---
 @pytest.mark.parametrize("g", [(3, -2), (0, 5), (-4, -4)])
 def test_com_of_phase_ramp_is_its_tilt(g):
@@ -187,6 +260,81 @@ def test_idpc_recovers_band_limited_phase():
     comy = gy / (2 * math.pi) * s
     out = orc.idpc(comx.ravel(), comy.ravel(), geom)
     np.testing.assert_allclose(out, phi - phi.mean(), atol=1e-10 * np.abs(phi).max())
+
+
+def _band_limited_com(Ny, Nx, st, w, seed=2, terms=12):
+    Y, X = np.mgrid[0:Ny, 0:Nx].astype(np.float64)
+    rng = np.random.default_rng(seed)
+    phi = np.zeros((Ny, Nx))
+    gx = np.zeros((Ny, Nx))
+    gy = np.zeros((Ny, Nx))
+    for _ in range(terms):
+        nx, ny = int(rng.integers(-Nx // 2 + 1, Nx // 2)), int(rng.integers(-Ny // 2 + 1, Ny // 2))
+        a, c = rng.normal(), rng.uniform(0, 2 * math.pi)
+        arg = 2 * math.pi * (nx * X / Nx + ny * Y / Ny) + c
+        phi += a * np.cos(arg)
+        gx += -a * np.sin(arg) * 2 * math.pi * nx / (Nx * st)
+        gy += -a * np.sin(arg) * 2 * math.pi * ny / (Ny * st)
+    s = w.lam / w.dalpha_raw
+    return phi, gx / (2 * math.pi) * s, gy / (2 * math.pi) * s
+
+
+def test_iterative_dpc_geometric_convergence():
+    """Without padding and regularisation each step removes the fraction mu
+    of the remaining error at every frequency: after L steps the literal
+    iteration equals (1 - (1 - mu)^L) (phi - mean phi), to 1e-10."""
+    w = synth.workload(1, scan_ny=24, scan_nx=40)
+    geom = synth.geometry(w)
+    phi, comx, comy = _band_limited_com(24, 40, w.step_A, w)
+    for L, mu in [(1, 0.5), (5, 0.5), (3, 1.0), (20, 0.3)]:
+        out = orc.dpc_iterative(comx.ravel(), comy.ravel(), geom, L, mu=mu, pad=1)
+        ref = (1 - (1 - mu) ** L) * (phi - phi.mean())
+        np.testing.assert_allclose(out, ref, atol=1e-10 * np.abs(phi).max())
+
+
+def test_iterative_dpc_regularised_per_frequency_factor():
+    """With lam1 > 0 the preconditioner 1/(lam1 + K^2) scales the step per
+    frequency: phi_L(K) = phi(K) (1 - (1 - mu K^2/(lam1 + K^2))^L), the
+    closed form of the linear recursion, to 1e-10."""
+    w = synth.workload(1, scan_ny=24, scan_nx=40)
+    geom = synth.geometry(w)
+    phi, comx, comy = _band_limited_com(24, 40, w.step_A, w, seed=5)
+    lam1, mu, L = 0.5, 0.5, 7
+    out = orc.dpc_iterative(comx.ravel(), comy.ravel(), geom, L, mu=mu, lam1=lam1, pad=1)
+    Kx = np.fft.fftfreq(40, d=w.step_A)[None, :]
+    Ky = np.fft.fftfreq(24, d=w.step_A)[:, None]
+    K2 = Kx * Kx + Ky * Ky
+    fac = np.zeros_like(K2)
+    nz = K2 > 0
+    fac[nz] = 1 - (1 - mu * K2[nz] / (lam1 + K2[nz])) ** L
+    ref = np.fft.ifft2(np.fft.fft2(phi) * fac).real
+    np.testing.assert_allclose(out, ref, atol=1e-10 * np.abs(phi).max())
+
+
+def test_iterative_dpc_padding_removes_wraparound():
+    """A tilted, non-periodic phase: the one-shot periodic integration cannot
+    represent the tilt, the zero-padded iteration with the residual on the
+    scan only does much better (error relative to phi - mean over the scan)."""
+    w = synth.workload(1, scan_ny=32, scan_nx=32)
+    geom = synth.geometry(w)
+    st = w.step_A
+    Y, X = np.mgrid[0:32, 0:32].astype(np.float64)
+    tilt = 0.15
+    bump = np.exp(-((X - 12.0) ** 2 + (Y - 20.0) ** 2) / (2 * 4.0 ** 2))
+    phi = tilt * X + 2.0 * bump
+    gx = (tilt + 2.0 * bump * (-(X - 12.0) / 4.0 ** 2)) / st
+    gy = (2.0 * bump * (-(Y - 20.0) / 4.0 ** 2)) / st
+    s = w.lam / w.dalpha_raw
+    comx, comy = gx / (2 * math.pi) * s, gy / (2 * math.pi) * s
+    ref = phi - phi.mean()
+
+    def err(a):
+        a = a - a.mean()
+        return np.linalg.norm(a - ref) / np.linalg.norm(ref)
+
+    e_closed = err(orc.idpc(comx.ravel(), comy.ravel(), geom))
+    e_iter = err(orc.dpc_iterative(comx.ravel(), comy.ravel(), geom, 100, mu=0.5, pad=2))
+    assert e_iter < 0.02 and e_closed > 0.5, (e_iter, e_closed)
 
 
 def test_idpc_sign_from_forward_model():
