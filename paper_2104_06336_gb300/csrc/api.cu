@@ -85,6 +85,7 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_lutx);
   cudaFree(p->d_luty);
   cudaFree(p->d_lut2);
+  cudaFree(p->d_lutp);
   cudaFree(p->d_pix);
   cudaFree(p->d_bfp);
   cudaFree(p->d_rows);
@@ -216,7 +217,24 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
     const long long v = d >= 0 ? d / g.bin : -1;
     luty[y] = (int16_t)((d >= 0 && v < (long long)g.ph) ? v : -1);
   }
+  // raw pixel -> kept pixel in one table (one lookup per event in the scatter)
+  std::vector<int16_t> lutp;
+  if ((uint64_t)g.det_w * g.det_h <= (1ull << 24)) {
+    lutp.assign((size_t)g.det_w * g.det_h, (int16_t)-1);
+    for (uint32_t y = 0; y < g.det_h; ++y) {
+      if (luty[y] < 0) continue;
+      for (uint32_t x = 0; x < g.det_w; ++x) {
+        if (lutx[x] < 0) continue;
+        lutp[(size_t)y * g.det_w + x] = (int16_t)lut2[(size_t)luty[y] * g.pw + lutx[x]];
+      }
+    }
+  }
   cudaError_t e;
+  if (!lutp.empty() && (e = upload(&p->d_lutp, lutp)) != cudaSuccess) {
+    const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
+    free_plan(p);
+    return rc;
+  }
   if ((e = upload(&p->d_lutx, lutx)) != cudaSuccess || (e = upload(&p->d_luty, luty)) != cudaSuccess ||
       (e = upload(&p->d_lut2, lut2)) != cudaSuccess || (e = upload(&p->d_pix, pix)) != cudaSuccess ||
       (e = upload(&p->d_bfp, bfp)) != cudaSuccess ||

@@ -60,6 +60,8 @@ struct eer4d_plan {
   int16_t* d_lutx;           // [det_w] binned u or -1
   int16_t* d_luty;           // [det_h] binned v or -1
   int32_t* d_lut2;           // [ph*pw] kept pixel index or -1
+  int16_t* d_lutp;           // [det_h*det_w] kept pixel of each raw pixel or -1 (NULL when
+                             // the detector has more than 2^24 pixels)
   short2* d_pix;             // [P_pad] (kx, ky)
   int32_t* d_bfp;            // [P_bf] kept-pixel index of each bright-field pixel (row-major)
   __half* d_dft_hi;          // split-FP16 DFT matrix along x (tile-blocked), SPLIT_FP16 plans

@@ -20,38 +20,6 @@ __device__ __forceinline__ void frame_range(const uint64_t* off, uint64_t f, uin
   bad = (b < a) || (b > n_idx) || (a > n_idx);
 }
 
-// Copies src[0..n) (global, uint32) into dst (shared) with 16-byte vector
-// loads for the aligned body, several loads in flight per thread.
-__device__ __forceinline__ void stage_u32(uint32_t* dst, const uint32_t* __restrict__ src, int n) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-  int head = (int)(((16 - (a & 15)) & 15) >> 2);
-  if ((a & 3) != 0) head = n;  // not even 4-byte aligned: all scalar
-  if (head > n) head = n;
-  for (int i = tid; i < head; i += nt) dst[i] = __ldg(src + i);
-  const int nv = (n - head) >> 2;
-  const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
-  int i = tid;
-  for (; i + 3 * nt < nv; i += 4 * nt) {
-    uint4 v0 = __ldg(s4 + i), v1 = __ldg(s4 + i + nt), v2 = __ldg(s4 + i + 2 * nt),
-          v3 = __ldg(s4 + i + 3 * nt);
-    uint32_t* d = dst + head;
-    d[4 * i + 0] = v0.x; d[4 * i + 1] = v0.y; d[4 * i + 2] = v0.z; d[4 * i + 3] = v0.w;
-    int j = i + nt;
-    d[4 * j + 0] = v1.x; d[4 * j + 1] = v1.y; d[4 * j + 2] = v1.z; d[4 * j + 3] = v1.w;
-    j += nt;
-    d[4 * j + 0] = v2.x; d[4 * j + 1] = v2.y; d[4 * j + 2] = v2.z; d[4 * j + 3] = v2.w;
-    j += nt;
-    d[4 * j + 0] = v3.x; d[4 * j + 1] = v3.y; d[4 * j + 2] = v3.z; d[4 * j + 3] = v3.w;
-  }
-  for (; i < nv; i += nt) {
-    uint4 v = __ldg(s4 + i);
-    uint32_t* d = dst + head + 4 * i;
-    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-  }
-  for (int k = head + 4 * nv + tid; k < n; k += nt) dst[k] = __ldg(src + k);
-}
-
 // ---------------------------------------------------------------- a1 -------
 // Offsets check, index range check, integer totals and optional PACBED.
 __global__ void __launch_bounds__(kThreads) k_validate(const uint32_t* __restrict__ idx,
@@ -122,30 +90,24 @@ __global__ void __launch_bounds__(kThreads) k_validate(const uint32_t* __restric
 }
 
 // ---------------------------------------------------------------- a2 -------
-// Per-frame integer sums, one thread per frame, events of the CTA's frames
-// staged in shared memory with vector loads (Eq. 4 on linear-index EER).
-constexpr int kComFrames = 256;
-constexpr int kComStage = 16384;
+// Per-frame integer sums (Eq. 4 on linear-index EER), one thread per frame.
+// A thread reads its frame's events straight from global memory, 16-byte
+// vector loads with four in flight (a frame's events are contiguous, so the
+// 32 frames of a warp cover one contiguous stretch of the event array and
+// every fetched sector is used); no shared staging and no block barrier
+// before the sums.  Thread 0 computes the centre meanwhile.
+constexpr int kComThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_com(const uint32_t* __restrict__ idx, uint64_t n_idx,
-                                                  const uint64_t* __restrict__ off, uint32_t F,
-                                                  uint32_t WH, DivMod dw,
-                                                  const long long* __restrict__ totals,
-                                                  double cx_h, double cy_h, float zscale,
-                                                  long long* sums, float* com, float2* z,
-                                                  uint32_t* st) {
-  extern __shared__ uint32_t ev[];
-  __shared__ unsigned long long s_lo, s_hi;
+__global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict__ idx, uint64_t n_idx,
+                                                     const uint64_t* __restrict__ off, uint32_t F,
+                                                     uint32_t WH, DivMod dw,
+                                                     const long long* __restrict__ totals,
+                                                     double cx_h, double cy_h, float zscale,
+                                                     long long* sums, float* com, float2* z,
+                                                     uint32_t* st) {
   __shared__ float s_cfx, s_cfy;
   __shared__ long long s_cix, s_ciy;
-  const uint32_t f0 = blockIdx.x * kComFrames;
-  const uint32_t f = f0 + threadIdx.x;
-  const bool have = f < F;
-  uint64_t lo = 0, hi = 0;
-  bool bad = false;
-  if (have) frame_range(off, f, n_idx, lo, hi, bad);
   if (threadIdx.x == 0) {
-    s_lo = ~0ull; s_hi = 0;
     // centre: integer part (exact) + fractional part (float), from double
     double cx = cx_h, cy = cy_h;
     if (totals) {
@@ -157,36 +119,42 @@ __global__ void __launch_bounds__(kThreads) k_com(const uint32_t* __restrict__ i
     s_cix = (long long)rx; s_ciy = (long long)ry;
     s_cfx = (float)(cx - rx); s_cfy = (float)(cy - ry);
   }
-  __syncthreads();
-  if (have && hi > lo) {
-    atomicMin(&s_lo, (unsigned long long)lo);
-    atomicMax(&s_hi, (unsigned long long)hi);
-  }
-  if (bad) st_or(st, EER4D_ST_OFFSETS);
-  __syncthreads();
-  const uint64_t E0 = s_lo, E1 = s_hi;
+  const uint32_t f = blockIdx.x * kComThreads + threadIdx.x;
   unsigned long long sx = 0, sy = 0, sn = 0;
   uint32_t drop = 0;
-  for (uint64_t base = E0; base < E1; base += kComStage) {
-    const int cnt = (int)min((uint64_t)kComStage, E1 - base);
-    __syncthreads();
-    stage_u32(ev, idx + base, cnt);
-    __syncthreads();
-    if (have) {
-      const uint64_t a = lo > base ? lo : base;
-      const uint64_t b = hi < base + cnt ? hi : base + cnt;
-      uint32_t px = 0, py = 0, pn = 0;
-      for (uint64_t i = a; i < b; ++i) {
-        const uint32_t v = ev[i - base];
-        if (v >= WH) { ++drop; continue; }
-        uint32_t y, x;
-        dw.divmod(v, y, x);
-        px += x; py += y; ++pn;
+  if (f < F) {
+    uint64_t lo, hi;
+    bool bad;
+    frame_range(off, f, n_idx, lo, hi, bad);
+    if (bad) st_or(st, EER4D_ST_OFFSETS);
+    uint32_t px = 0, py = 0, pn = 0;
+    auto one = [&](uint32_t v) {
+      if (v >= WH) { ++drop; return; }
+      uint32_t y, x;
+      dw.divmod(v, y, x);
+      px += x; py += y; ++pn;
+    };
+    uint64_t i = lo;
+    if ((reinterpret_cast<uintptr_t>(idx) & 15) == 0) {
+      for (; i < hi && (i & 3); ++i) one(__ldg(idx + i));
+      for (; i + 16 <= hi; i += 16) {
+        const uint4* q = reinterpret_cast<const uint4*>(idx + i);
+        const uint4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+        one(a0.x); one(a0.y); one(a0.z); one(a0.w);
+        one(a1.x); one(a1.y); one(a1.z); one(a1.w);
+        one(a2.x); one(a2.y); one(a2.z); one(a2.w);
+        one(a3.x); one(a3.y); one(a3.z); one(a3.w);
       }
-      sx += px; sy += py; sn += pn;
+      for (; i + 4 <= hi; i += 4) {
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4*>(idx + i));
+        one(a0.x); one(a0.y); one(a0.z); one(a0.w);
+      }
     }
+    for (; i < hi; ++i) one(__ldg(idx + i));
+    sx = px; sy = py; sn = pn;
   }
-  if (have) {
+  __syncthreads();  // the centre
+  if (f < F) {
     sums[f] = (long long)sx;
     sums[F + f] = (long long)sy;
     sums[2 * (size_t)F + f] = (long long)sn;
@@ -214,101 +182,137 @@ __global__ void __launch_bounds__(kThreads) k_com(const uint32_t* __restrict__ i
 // tile of packed 16-bit counters (two frames per word, rows padded by one word
 // so the pixels of a frame fall in different banks), then writes
 // counts[p][f] as fp16, four frames per 8-byte store.  No global atomics;
-// every (p, f) of the chunk is written exactly once, zeros included.  The
-// tile is kept small (<= 48 KB) so several CTAs overlap their phases.
-constexpr int kScatStage = 4096;
+// every (p, f) of the chunk is written exactly once, zeros included.  Events
+// are read straight from global memory, a warp per pair of frames with its
+// lanes on consecutive events (128-byte loads, four in flight per lane), and
+// mapped to a kept pixel by one table lookup (raw pixel -> kept pixel).
 constexpr int kMaxFrameEvents = 65535;
 
 __global__ void __launch_bounds__(kThreads) k_scatter(
     const uint32_t* __restrict__ idx, uint64_t n_idx, const uint64_t* __restrict__ off,
-    uint64_t first, uint64_t nfr, uint32_t WH, DivMod dw, const int16_t* __restrict__ lutx,
-    const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int P_pad, int TF,
-    uint64_t NR, __half* counts, uint32_t* st) {
-  extern __shared__ uint32_t smem[];
-  __shared__ uint32_t s_lo[128], s_hi[128];  // event range of each tile frame, relative to E0
-  __shared__ unsigned long long s_e0, s_e1;
+    uint64_t first, uint64_t nfr, uint32_t WH, DivMod dw, const int16_t* __restrict__ lutp,
+    const int16_t* __restrict__ lutx, const int16_t* __restrict__ luty,
+    const int32_t* __restrict__ lut2, int pw, int P_pad, int TF, uint64_t NR, __half* counts,
+    uint32_t* st) {
+  extern __shared__ uint32_t tile[];           // [P_pad][TP]
+  __shared__ unsigned long long s_lo[128];     // event range of each tile frame
+  __shared__ uint32_t s_n[128];
+  __shared__ uint32_t s_maxev;                 // most events in one frame of the tile
   const int TW = TF / 2;
   const int TP = TW + 1;
-  uint32_t* tile = smem;                     // [P_pad][TP]
-  uint32_t* ev = smem + (size_t)P_pad * TP;  // [kScatStage]
   const uint64_t T0 = (first / TF) * TF;
   const uint64_t tf0 = T0 + (uint64_t)blockIdx.x * TF;  // global frame of tile column 0
   const uint64_t end = first + nfr;
   // frames j of the tile inside the chunk: [j0, j1)
   const int j0 = tf0 < first ? (int)(first - tf0) : 0;
   const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
+  if (threadIdx.x == 0) s_maxev = 0;
   {
     uint4* t4 = reinterpret_cast<uint4*>(tile);  // P_pad * TP is a multiple of 4 (P_pad % 16 == 0)
     const int n4 = P_pad * TP / 4;
     for (int i = threadIdx.x; i < n4; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
   }
-  if (threadIdx.x == 0) { s_e0 = ~0ull; s_e1 = 0; }
   __syncthreads();
-  bool bad = false;
-  uint64_t lo = 0, hi = 0;
-  if (threadIdx.x >= j0 && threadIdx.x < j1) {
-    bool b;
-    frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
-    bad |= b;
-    if (hi - lo > kMaxFrameEvents) { bad = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
-    if (hi > lo) { atomicMin(&s_e0, (unsigned long long)lo); atomicMax(&s_e1, (unsigned long long)hi); }
+  if (threadIdx.x < TF) {
+    uint64_t lo = 0, hi = 0;
+    bool b = false;
+    if (threadIdx.x >= j0 && threadIdx.x < j1) {
+      frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
+      if (hi - lo > kMaxFrameEvents) { b = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
+      if (b) st_or(st, EER4D_ST_OFFSETS);
+    }
+    s_lo[threadIdx.x] = lo;
+    s_n[threadIdx.x] = (uint32_t)(hi - lo);
+    if (hi > lo) atomicMax(&s_maxev, (uint32_t)(hi - lo));
   }
-  if (bad) st_or(st, EER4D_ST_OFFSETS);
   __syncthreads();
-  const uint64_t E0 = s_e0, E1 = s_e1;
-  if (threadIdx.x < TF) {  // 32-bit event offsets relative to E0 (a tile spans < 2^32 events)
-    const bool in = threadIdx.x >= j0 && threadIdx.x < j1 && hi > lo;
-    s_lo[threadIdx.x] = in ? (uint32_t)(lo - E0) : 0u;
-    s_hi[threadIdx.x] = in ? (uint32_t)(hi - E0) : 0u;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   uint32_t drop = 0;
-  const uint32_t nev = E1 > E0 ? (uint32_t)(E1 - E0) : 0u;
-  for (uint32_t base = 0; base < nev; base += kScatStage) {
-    const int cnt = (int)min((uint32_t)kScatStage, nev - base);
-    __syncthreads();
-    stage_u32(ev, idx + E0 + base, cnt);
-    __syncthreads();
-    for (int j = j0 + warp; j < j1; j += nw) {
-      const uint32_t a = max(s_lo[j], base), e = min(s_hi[j], base + (uint32_t)cnt);
-      const uint32_t inc = 1u << (16 * (j & 1));
-      uint32_t* col = tile + (j >> 1);
-      for (uint32_t i = a + lane; i < e; i += 32) {
-        const uint32_t v = ev[i - base];
-        if (v >= WH) { ++drop; continue; }
-        uint32_t y, x;
-        dw.divmod(v, y, x);
-        const int u = __ldg(lutx + x), vv = __ldg(luty + y);
-        if ((u | vv) < 0) continue;
-        const int p = __ldg(lut2 + vv * pw + u);
-        if (p < 0) continue;
-        atomicAdd(col + p * TP, inc);
-      }
+  auto pixel = [&](uint32_t v) -> int {
+    if (lutp) return __ldg(lutp + v);
+    uint32_t y, x;
+    dw.divmod(v, y, x);
+    const int u = __ldg(lutx + x), vv = __ldg(luty + y);
+    if ((u | vv) < 0) return -1;
+    return __ldg(lut2 + vv * pw + u);
+  };
+  for (int ja = j0 + warp; ja < j1; ja += 2 * nw) {
+    const int jb = ja + nw;  // second frame of the pair (may be past j1)
+    const uint64_t la = s_lo[ja];
+    const uint32_t na = s_n[ja];
+    const uint64_t lb = jb < j1 ? s_lo[jb] : 0;
+    const uint32_t nb = jb < j1 ? s_n[jb] : 0u;
+    const uint32_t inca = 1u << (16 * (ja & 1)), incb = 1u << (16 * (jb & 1));
+    uint32_t* cola = tile + (ja >> 1);
+    uint32_t* colb = tile + (jb >> 1);
+    const uint32_t nmax = na > nb ? na : nb;
+    for (uint32_t k = lane; k < nmax; k += 64) {
+      // up to four independent loads per lane before any is used
+      const bool a0 = k < na, a1 = k + 32 < na, b0 = k < nb, b1 = k + 32 < nb;
+      const uint32_t va0 = a0 ? __ldg(idx + la + k) : WH;
+      const uint32_t va1 = a1 ? __ldg(idx + la + k + 32) : WH;
+      const uint32_t vb0 = b0 ? __ldg(idx + lb + k) : WH;
+      const uint32_t vb1 = b1 ? __ldg(idx + lb + k + 32) : WH;
+      drop += (a0 && va0 >= WH) + (a1 && va1 >= WH) + (b0 && vb0 >= WH) + (b1 && vb1 >= WH);
+      const int pa0 = va0 < WH ? pixel(va0) : -1;
+      const int pa1 = va1 < WH ? pixel(va1) : -1;
+      const int pb0 = vb0 < WH ? pixel(vb0) : -1;
+      const int pb1 = vb1 < WH ? pixel(vb1) : -1;
+      if (pa0 >= 0) atomicAdd(cola + pa0 * TP, inca);
+      if (pa1 >= 0) atomicAdd(cola + pa1 * TP, inca);
+      if (pb0 >= 0) atomicAdd(colb + pb0 * TP, incb);
+      if (pb1 >= 0) atomicAdd(colb + pb1 * TP, incb);
     }
   }
   __syncthreads();
   // write counts[p][tf0 + 4w .. tf0 + 4w + 3] (two tile words, four fp16) per lane
   uint32_t over = 0;
   const bool full = j0 == 0 && j1 == TF;
-  const int QW = TW / 2;  // 8-byte groups per pixel row
-  for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
-    const int p = i / QW, w = i - p * QW;
-    const uint32_t w0 = tile[p * TP + 2 * w], w1 = tile[p * TP + 2 * w + 1];
-    const uint32_t c0 = w0 & 0xffffu, c1 = w0 >> 16, c2 = w1 & 0xffffu, c3 = w1 >> 16;
-    over += (c0 > 2048u) + (c1 > 2048u) + (c2 > 2048u) + (c3 > 2048u);
-    const __half2 h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
-    const __half2 h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
-    __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
-    if (full) {
-      uint2 pk;
-      pk.x = *reinterpret_cast<const uint32_t*>(&h01);
-      pk.y = *reinterpret_cast<const uint32_t*>(&h23);
-      *reinterpret_cast<uint2*>(dst) = pk;
-    } else {
-      const __half hv[4] = {__low2half(h01), __high2half(h01), __low2half(h23), __high2half(h23)};
-      for (int k = 0; k < 4; ++k) {
-        const int j = 4 * w + k;
-        if (j >= j0 && j < j1) dst[k] = hv[k];
+  const int QW = TW / 2;  // 8-byte groups per pixel row (a power of two)
+  const int qs = __ffs(QW) - 1;
+  if (s_maxev < 1024u) {
+    // every count is below 1024: OR-ing 0x6400 (fp16 1024.0) into a 16-bit
+    // count n gives the fp16 of 1024 + n exactly; subtracting 1024 gives n
+    const __half2 k1024 = __floats2half2_rn(1024.f, 1024.f);
+    for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
+      const int p = i >> qs, w = i & (QW - 1);
+      const uint32_t w0 = tile[p * TP + 2 * w] | 0x64006400u, w1 = tile[p * TP + 2 * w + 1] | 0x64006400u;
+      const __half2 h01 = __hsub2(*reinterpret_cast<const __half2*>(&w0), k1024);
+      const __half2 h23 = __hsub2(*reinterpret_cast<const __half2*>(&w1), k1024);
+      __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
+      if (full) {
+        uint2 pk;
+        pk.x = *reinterpret_cast<const uint32_t*>(&h01);
+        pk.y = *reinterpret_cast<const uint32_t*>(&h23);
+        *reinterpret_cast<uint2*>(dst) = pk;
+      } else {
+        const __half hv[4] = {__low2half(h01), __high2half(h01), __low2half(h23), __high2half(h23)};
+        for (int k = 0; k < 4; ++k) {
+          const int j = 4 * w + k;
+          if (j >= j0 && j < j1) dst[k] = hv[k];
+        }
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
+      const int p = i >> qs, w = i & (QW - 1);
+      const uint32_t w0 = tile[p * TP + 2 * w], w1 = tile[p * TP + 2 * w + 1];
+      const uint32_t c0 = w0 & 0xffffu, c1 = w0 >> 16, c2 = w1 & 0xffffu, c3 = w1 >> 16;
+      over += (c0 > 2048u) + (c1 > 2048u) + (c2 > 2048u) + (c3 > 2048u);
+      const __half2 h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
+      const __half2 h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
+      __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
+      if (full) {
+        uint2 pk;
+        pk.x = *reinterpret_cast<const uint32_t*>(&h01);
+        pk.y = *reinterpret_cast<const uint32_t*>(&h23);
+        *reinterpret_cast<uint2*>(dst) = pk;
+      } else {
+        const __half hv[4] = {__low2half(h01), __high2half(h01), __low2half(h23), __high2half(h23)};
+        for (int k = 0; k < 4; ++k) {
+          const int j = 4 * w + k;
+          if (j >= j0 && j < j1) dst[k] = hv[k];
+        }
       }
     }
   }
@@ -337,7 +341,13 @@ cudaError_t launch_validate(const eer4d_plan* p, const uint32_t* idx, uint64_t n
                             int64_t* totals, uint32_t* st, cudaStream_t s) {
   const uint64_t work = n_frames > n_idx / 16 ? n_frames : n_idx / 16;
   uint64_t blocks = (work + kThreads - 1) / kThreads;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  // SMs x resident CTAs: one full wave, no partial second wave
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_validate, kThreads, 0);
+  const uint64_t wave = (uint64_t)nsm * (occ > 0 ? occ : 1);
+  if (blocks > wave) blocks = wave;
   if (blocks == 0) blocks = 1;
   stage_begin(p, EER4D_STAGE_VALIDATE, s);
   k_validate<<<(unsigned)blocks, kThreads, 0, s>>>(
@@ -353,12 +363,9 @@ cudaError_t launch_com(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                        int64_t* sums, float* com, float2* z, const int64_t* totals, double cx,
                        double cy, uint32_t* st, cudaStream_t s) {
   const uint32_t F = (uint32_t)p->F;
-  const size_t sm = kComStage * sizeof(uint32_t);
-  cudaError_t e = ensure_smem((const void*)k_com, sm);
-  if (e != cudaSuccess) return e;
   const float zscale = (float)(p->g.dalpha_raw_rad / p->g.lambda_A);
   stage_begin(p, EER4D_STAGE_COM, s);
-  k_com<<<(F + kComFrames - 1) / kComFrames, kThreads, sm, s>>>(
+  k_com<<<(F + kComThreads - 1) / kComThreads, kComThreads, 0, s>>>(
       idx, n_idx, off, F, p->g.det_w * p->g.det_h, p->dw,
       reinterpret_cast<const long long*>(totals), cx, cy, zscale,
       reinterpret_cast<long long*>(sums), com, z, st);
@@ -372,14 +379,15 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
                            uint32_t* st, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int TF = scatter_tf(p->P_pad);
-  const size_t sm = (size_t)p->P_pad * (TF / 2 + 1) * 4 + kScatStage * 4;
+  const size_t sm = (size_t)p->P_pad * (TF / 2 + 1) * 4;
   cudaError_t e = ensure_smem((const void*)k_scatter, sm);
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;
   const uint64_t tiles = (first + n - T0 + TF - 1) / TF;
   stage_begin(p, EER4D_STAGE_SCATTER, s);
   k_scatter<<<(unsigned)tiles, kThreads, sm, s>>>(
-      idx, n_idx, off, first, n, p->g.det_w * p->g.det_h, p->dw, p->d_lutx, p->d_luty, p->d_lut2,
+      idx, n_idx, off, first, n, p->g.det_w * p->g.det_h, p->dw, p->d_lutp, p->d_lutx, p->d_luty,
+      p->d_lut2,
       (int)p->g.pw, p->P_pad, TF, (uint64_t)p->F, counts, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_SCATTER, s);
