@@ -102,7 +102,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t work_counts_bytes(const eer4d_plan* p) { return (size_t)2 * p->P_pad * p->F; }
+size_t work_counts_bytes(const eer4d_plan* p) { return (size_t)2 * p->P_pad * p->cstride; }
 size_t work_bytes(const eer4d_plan* p) {
   if (dft2_fused_ok(p)) return al256(work_counts_bytes(p)) + al256(dft2_ring_bytes(p)) + dft2_ctl_bytes(p);
   return al256(work_counts_bytes(p)) + sizeof(float2) * (size_t)p->nkx * p->g.scan_ny * p->P_pad;
@@ -161,6 +161,10 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   p->precision = precision;
   p->norm = norm;
   p->F = (int)(g.scan_ny * g.scan_nx);
+#ifndef EER4D_COUNTS_PAD
+#define EER4D_COUNTS_PAD 0
+#endif
+  p->cstride = (long long)p->F + EER4D_COUNTS_PAD;
   p->nkx = (int)g.scan_nx / 2 + 1;
   p->dw.init(g.det_w);
 

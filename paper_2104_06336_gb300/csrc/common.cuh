@@ -55,6 +55,7 @@ struct eer4d_plan {
   int precision, norm;
   int P, P_pad, P_bf, n_rows, nkx, list_max;
   int F;
+  long long cstride;         // row stride (elements) of the fp16 counts [P_pad][cstride]
   DivMod dw;                 // division by det_w
   // device tables (owned)
   int16_t* d_lutx;           // [det_w] binned u or -1

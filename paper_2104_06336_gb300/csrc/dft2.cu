@@ -37,7 +37,7 @@ struct Dft2Params {
   int N, nkx, P_pad, gp, n_groups, n1, n2;
   long long slot;   // float2 per ring slot
   long long total;  // tasks
-  long long F;      // frames
+  long long F;      // row stride of the counts (frames, padded)
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -214,7 +214,7 @@ cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, fl
   q.n2 = p->nkx;
   q.slot = (long long)p->nkx * N * q.gp;
   q.total = (long long)q.n_groups * (q.n1 + q.n2);
-  q.F = (long long)N * N;
+  q.F = p->cstride;
   if ((e = cudaMemsetAsync(ctl, 0, ctl_bytes, s)) != cudaSuccess) return e;
   long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
   if (grid > q.total) grid = q.total;

@@ -485,13 +485,14 @@ cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* 
   const int KT = (Nx + kK - 1) / kK;
   const int NT = (2 * p->nkx + kN - 1) / kN;
   const long long NR = (long long)Ny * Nx;
+  const long long CS = p->cstride;  // counts row stride
   // pipelined TMA form when its alignment rules hold: x coordinates (frames)
-  // at multiples of 8 fp16 (16 bytes), row stride NR*2 a multiple of 16
+  // at multiples of 8 fp16 (16 bytes), row stride CS*2 a multiple of 16
   EncodeTiledFn enc = encode_fn();
-  if (enc && Nx % 8 == 0 && NR % 8 == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
+  if (enc && Nx % 8 == 0 && CS % 8 == 0 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)NR, (cuuint64_t)p->P_pad};
-    const cuuint64_t gstride[1] = {(cuuint64_t)NR * 2};
+    const cuuint64_t gstride[1] = {(cuuint64_t)CS * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kK, (cuuint32_t)kM};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(counts), gdim, gstride,
@@ -513,7 +514,7 @@ cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* 
       return cudaGetLastError();
     }
   }
-  const int vec = (Nx % 8 == 0) && (NR % 8 == 0);
+  const int vec = (Nx % 8 == 0) && (CS % 8 == 0);
   const size_t smem = kTileA + 2 * kTileB;
   cudaError_t e = ensure_smem((const void*)k_dftx_tc, smem);
   if (e != cudaSuccess) return e;
@@ -521,7 +522,7 @@ cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* 
   stage_begin(p, EER4D_STAGE_DFT_X, s);
   k_dftx_tc<<<grid, kThreadsTC, smem, s>>>(counts, reinterpret_cast<const uint4*>(p->d_dft_hi),
                                            reinterpret_cast<const uint4*>(p->d_dft_lo), X1, Nx, KT,
-                                           NT, p->nkx, p->P_pad, Ny, NR, y0, vec, st);
+                                           NT, p->nkx, p->P_pad, Ny, CS, y0, vec, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_DFT_X, s);
   return cudaGetLastError();

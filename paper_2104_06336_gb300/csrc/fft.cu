@@ -313,7 +313,7 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
                           cudaStream_t s) {
   if (y1 <= y0) return cudaSuccess;
   const FftDesc& d = p->fx;
-  const long long NRl = (long long)p->g.scan_ny * p->g.scan_nx;
+  const long long NRl = p->cstride;
   if (reg_size(d.N)) {
     stage_begin(p, EER4D_STAGE_DFT_X, s);
     cudaError_t e = r2c_reg(d, counts, G, p->P_pad, y0, y1 - y0, NRl, (long long)p->g.scan_nx,
@@ -326,7 +326,7 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
   const size_t sm = (size_t)2 * nb * d.N * sizeof(float2);
   cudaError_t e = set_smem(k_rows_r2c<__half>, sm);
   if (e != cudaSuccess) return e;
-  const long long NR = (long long)p->g.scan_ny * p->g.scan_nx;
+  const long long NR = p->cstride;
   dim3 grid((p->P_pad + TA - 1) / TA, y1 - y0);
   stage_begin(p, EER4D_STAGE_DFT_X, s);
   k_rows_r2c<__half><<<grid, kThreads, sm, s>>>(

@@ -177,130 +177,145 @@ __global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict_
 }
 
 // ---------------------------------------------------------------- a4 -------
-// Bin + crop + densify.  A CTA owns TF consecutive frames (aligned to
-// multiples of TF in the scan) and all P_pad pixels: it counts into a shared
-// tile of packed 16-bit counters (two frames per word, rows padded by one word
-// so the pixels of a frame fall in different banks), then writes
-// counts[p][f] as fp16, four frames per 8-byte store.  No global atomics;
-// every (p, f) of the chunk is written exactly once, zeros included.  Events
-// are read straight from global memory, a warp per pair of frames with its
-// lanes on consecutive events (128-byte loads, four in flight per lane), and
-// mapped to a kept pixel by one table lookup (raw pixel -> kept pixel).
+// Bin + crop + densify.  A persistent CTA takes tiles of TF consecutive frames
+// (aligned to multiples of TF in the scan) and all P_pad pixels: it counts
+// into a shared tile of packed 16-bit counters (two frames per word, rows
+// padded by one word so the pixels of a frame fall in different banks), then
+// writes counts[p][f] as fp16, four frames per 8-byte store.  No global
+// atomics; every (p, f) of the chunk is written exactly once, zeros included.
+// Events are read straight from global memory, a warp per four frames with its
+// lanes on consecutive events (128-byte loads, eight in flight per lane).
+// The pixel of an event comes from the binning tables x -> u, y -> v and
+// (v, u) -> kept pixel, copied once per CTA into shared memory (one divide
+// by det_w and three shared loads, no L2 round trip per event); detectors
+// whose tables do not fit use the raw-pixel table (or the three tables) in
+// global memory.
 constexpr int kMaxFrameEvents = 65535;
 
-__global__ void __launch_bounds__(kThreads) k_scatter(
+__global__ void __launch_bounds__(kThreads, 2) k_scatter(
     const uint32_t* __restrict__ idx, uint64_t n_idx, const uint64_t* __restrict__ off,
-    uint64_t first, uint64_t nfr, uint32_t WH, DivMod dw, const int16_t* __restrict__ lutp,
-    const int16_t* __restrict__ lutx, const int16_t* __restrict__ luty,
-    const int32_t* __restrict__ lut2, int pw, int P_pad, int TF, uint64_t NR, __half* counts,
-    uint32_t* st) {
-  extern __shared__ uint32_t tile[];           // [P_pad][TP]
-  __shared__ unsigned long long s_lo[128];     // event range of each tile frame
+    uint64_t first, uint64_t nfr, uint32_t W, uint32_t H, DivMod dw,
+    const int16_t* __restrict__ lutp, const int16_t* __restrict__ lutx,
+    const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int ph, int P_pad,
+    int TF, uint64_t ntiles, int tab_smem, uint64_t NR, __half* counts, uint32_t* st) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long s_lo[128];  // event range of each tile frame
   __shared__ uint32_t s_n[128];
-  __shared__ uint32_t s_maxev;                 // most events in one frame of the tile
+  __shared__ uint32_t s_maxev;              // most events in one frame of the tile
+  const uint32_t WH = W * H;
   const int TW = TF / 2;
   const int TP = TW + 1;
-  const uint64_t T0 = (first / TF) * TF;
-  const uint64_t tf0 = T0 + (uint64_t)blockIdx.x * TF;  // global frame of tile column 0
-  const uint64_t end = first + nfr;
-  // frames j of the tile inside the chunk: [j0, j1)
-  const int j0 = tf0 < first ? (int)(first - tf0) : 0;
-  const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
-  if (threadIdx.x == 0) s_maxev = 0;
-  {
-    uint4* t4 = reinterpret_cast<uint4*>(tile);  // P_pad * TP is a multiple of 4 (P_pad % 16 == 0)
-    const int n4 = P_pad * TP / 4;
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t* tile = smem;  // [P_pad][TP]
+  int16_t* tx = reinterpret_cast<int16_t*>(smem + (size_t)P_pad * TP);  // [W], [H], [ph*pw]
+  int16_t* ty = tx + W;
+  int16_t* t2 = ty + H;
+  if (tab_smem) {
+    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) tx[i] = lutx[i];
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) ty[i] = luty[i];
+    for (int i = threadIdx.x; i < pw * ph; i += blockDim.x) t2[i] = (int16_t)lut2[i];
   }
-  __syncthreads();
-  if (threadIdx.x < TF) {
-    uint64_t lo = 0, hi = 0;
-    bool b = false;
-    if (threadIdx.x >= j0 && threadIdx.x < j1) {
-      frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
-      if (hi - lo > kMaxFrameEvents) { b = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
-      if (b) st_or(st, EER4D_ST_OFFSETS);
-    }
-    s_lo[threadIdx.x] = lo;
-    s_n[threadIdx.x] = (uint32_t)(hi - lo);
-    if (hi > lo) atomicMax(&s_maxev, (uint32_t)(hi - lo));
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  uint32_t drop = 0;
   auto pixel = [&](uint32_t v) -> int {
+    if (tab_smem) {
+      uint32_t y, x;
+      dw.divmod(v, y, x);
+      const int u = tx[x], vv = ty[y];
+      return (u | vv) < 0 ? -1 : t2[vv * pw + u];
+    }
     if (lutp) return __ldg(lutp + v);
     uint32_t y, x;
     dw.divmod(v, y, x);
     const int u = __ldg(lutx + x), vv = __ldg(luty + y);
-    if ((u | vv) < 0) return -1;
-    return __ldg(lut2 + vv * pw + u);
+    return (u | vv) < 0 ? -1 : __ldg(lut2 + vv * pw + u);
   };
-  for (int ja = j0 + warp; ja < j1; ja += 2 * nw) {
-    const int jb = ja + nw;  // second frame of the pair (may be past j1)
-    const uint64_t la = s_lo[ja];
-    const uint32_t na = s_n[ja];
-    const uint64_t lb = jb < j1 ? s_lo[jb] : 0;
-    const uint32_t nb = jb < j1 ? s_n[jb] : 0u;
-    const uint32_t inca = 1u << (16 * (ja & 1)), incb = 1u << (16 * (jb & 1));
-    uint32_t* cola = tile + (ja >> 1);
-    uint32_t* colb = tile + (jb >> 1);
-    const uint32_t nmax = na > nb ? na : nb;
-    for (uint32_t k = lane; k < nmax; k += 64) {
-      // up to four independent loads per lane before any is used
-      const bool a0 = k < na, a1 = k + 32 < na, b0 = k < nb, b1 = k + 32 < nb;
-      const uint32_t va0 = a0 ? __ldg(idx + la + k) : WH;
-      const uint32_t va1 = a1 ? __ldg(idx + la + k + 32) : WH;
-      const uint32_t vb0 = b0 ? __ldg(idx + lb + k) : WH;
-      const uint32_t vb1 = b1 ? __ldg(idx + lb + k + 32) : WH;
-      drop += (a0 && va0 >= WH) + (a1 && va1 >= WH) + (b0 && vb0 >= WH) + (b1 && vb1 >= WH);
-      const int pa0 = va0 < WH ? pixel(va0) : -1;
-      const int pa1 = va1 < WH ? pixel(va1) : -1;
-      const int pb0 = vb0 < WH ? pixel(vb0) : -1;
-      const int pb1 = vb1 < WH ? pixel(vb1) : -1;
-      if (pa0 >= 0) atomicAdd(cola + pa0 * TP, inca);
-      if (pa1 >= 0) atomicAdd(cola + pa1 * TP, inca);
-      if (pb0 >= 0) atomicAdd(colb + pb0 * TP, incb);
-      if (pb1 >= 0) atomicAdd(colb + pb1 * TP, incb);
-    }
-  }
-  __syncthreads();
-  // write counts[p][tf0 + 4w .. tf0 + 4w + 3] (two tile words, four fp16) per lane
-  uint32_t over = 0;
-  const bool full = j0 == 0 && j1 == TF;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  uint32_t drop = 0, over = 0;
+  const uint64_t T0 = (first / TF) * TF;
+  const uint64_t end = first + nfr;
   const int QW = TW / 2;  // 8-byte groups per pixel row (a power of two)
   const int qs = __ffs(QW) - 1;
-  if (s_maxev < 1024u) {
-    // every count is below 1024: OR-ing 0x6400 (fp16 1024.0) into a 16-bit
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t tf0 = T0 + t * TF;  // global frame of tile column 0
+    // frames j of the tile inside the chunk: [j0, j1)
+    const int j0 = tf0 < first ? (int)(first - tf0) : 0;
+    const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
+    __syncthreads();  // the previous tile is written out
+    if (threadIdx.x == 0) s_maxev = 0;
+    {
+      uint4* t4 = reinterpret_cast<uint4*>(tile);  // P_pad * TP is a multiple of 4 (P_pad % 16 == 0)
+      const int n4 = P_pad * TP / 4;
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    if (threadIdx.x < TF) {
+      uint64_t lo = 0, hi = 0;
+      bool b = false;
+      if (threadIdx.x >= j0 && threadIdx.x < j1) {
+        frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
+        if (hi - lo > kMaxFrameEvents) { b = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
+        if (b) st_or(st, EER4D_ST_OFFSETS);
+      }
+      s_lo[threadIdx.x] = lo;
+      s_n[threadIdx.x] = (uint32_t)(hi - lo);
+      if (hi > lo) atomicMax(&s_maxev, (uint32_t)(hi - lo));
+    }
+    __syncthreads();
+    // a warp takes four frames at a time (j, j + nw, j + 2 nw, j + 3 nw) and
+    // issues the loads of all four before using any (eight in flight per lane)
+    for (int jg = j0 + warp; jg < j1; jg += 4 * nw) {
+      uint64_t lo4[4];
+      uint32_t n4[4], nmax = 0;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int j = jg + f * nw;
+        lo4[f] = j < j1 ? s_lo[j] : 0;
+        n4[f] = j < j1 ? s_n[j] : 0u;
+        nmax = n4[f] > nmax ? n4[f] : nmax;
+      }
+      for (uint32_t k = lane; k < nmax; k += 64) {
+        uint32_t v[8];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          v[2 * f] = k < n4[f] ? __ldg(idx + lo4[f] + k) : WH;
+          v[2 * f + 1] = k + 32 < n4[f] ? __ldg(idx + lo4[f] + k + 32) : WH;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int j = jg + f * nw;
+          const uint32_t inc = 1u << (16 * (j & 1));
+          uint32_t* col = tile + (j >> 1);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t kk = k + 32 * h;
+            if (kk >= n4[f]) continue;
+            const uint32_t e = v[2 * f + h];
+            if (e >= WH) { ++drop; continue; }
+            const int pp = pixel(e);
+            if (pp >= 0) atomicAdd(col + pp * TP, inc);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // write counts[p][tf0 + 4w .. tf0 + 4w + 3] (two tile words, four fp16) per lane
+    const bool full = j0 == 0 && j1 == TF;
+    const bool small = s_maxev < 1024u;
+    // with every count below 1024, OR-ing 0x6400 (fp16 1024.0) into a 16-bit
     // count n gives the fp16 of 1024 + n exactly; subtracting 1024 gives n
     const __half2 k1024 = __floats2half2_rn(1024.f, 1024.f);
     for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
       const int p = i >> qs, w = i & (QW - 1);
-      const uint32_t w0 = tile[p * TP + 2 * w] | 0x64006400u, w1 = tile[p * TP + 2 * w + 1] | 0x64006400u;
-      const __half2 h01 = __hsub2(*reinterpret_cast<const __half2*>(&w0), k1024);
-      const __half2 h23 = __hsub2(*reinterpret_cast<const __half2*>(&w1), k1024);
-      __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
-      if (full) {
-        uint2 pk;
-        pk.x = *reinterpret_cast<const uint32_t*>(&h01);
-        pk.y = *reinterpret_cast<const uint32_t*>(&h23);
-        *reinterpret_cast<uint2*>(dst) = pk;
-      } else {
-        const __half hv[4] = {__low2half(h01), __high2half(h01), __low2half(h23), __high2half(h23)};
-        for (int k = 0; k < 4; ++k) {
-          const int j = 4 * w + k;
-          if (j >= j0 && j < j1) dst[k] = hv[k];
-        }
-      }
-    }
-  } else {
-    for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
-      const int p = i >> qs, w = i & (QW - 1);
       const uint32_t w0 = tile[p * TP + 2 * w], w1 = tile[p * TP + 2 * w + 1];
-      const uint32_t c0 = w0 & 0xffffu, c1 = w0 >> 16, c2 = w1 & 0xffffu, c3 = w1 >> 16;
-      over += (c0 > 2048u) + (c1 > 2048u) + (c2 > 2048u) + (c3 > 2048u);
-      const __half2 h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
-      const __half2 h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
+      __half2 h01, h23;
+      if (small) {
+        const uint32_t m0 = w0 | 0x64006400u, m1 = w1 | 0x64006400u;
+        h01 = __hsub2(*reinterpret_cast<const __half2*>(&m0), k1024);
+        h23 = __hsub2(*reinterpret_cast<const __half2*>(&m1), k1024);
+      } else {
+        const uint32_t c0 = w0 & 0xffffu, c1 = w0 >> 16, c2 = w1 & 0xffffu, c3 = w1 >> 16;
+        over += (c0 > 2048u) + (c1 > 2048u) + (c2 > 2048u) + (c3 > 2048u);
+        h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
+        h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
+      }
       __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
       if (full) {
         uint2 pk;
@@ -329,10 +344,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
 }  // namespace
 
 // frames per scatter tile: a multiple of 4 (8-byte count stores), at most
-// 128, with the padded tile P_pad x (TF/2 + 1) words within 48 KB
+// 128, with the padded tile P_pad x (TF/2 + 1) words within the tile budget
+#ifndef EER4D_SCATTER_TILE_KB
+#define EER4D_SCATTER_TILE_KB 40
+#endif
+constexpr size_t kScatterTabBytes = 64 * 1024;  // largest binning tables kept in shared memory
 int scatter_tf(int P_pad) {
   int tf = 128;
-  while (tf > 4 && (size_t)P_pad * (tf / 2 + 1) * 4 > 48 * 1024) tf >>= 1;
+  while (tf > 4 && (size_t)P_pad * (tf / 2 + 1) * 4 > EER4D_SCATTER_TILE_KB * 1024) tf >>= 1;
   return tf;
 }
 
@@ -379,16 +398,27 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
                            uint32_t* st, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int TF = scatter_tf(p->P_pad);
-  const size_t sm = (size_t)p->P_pad * (TF / 2 + 1) * 4;
+  const uint32_t W = p->g.det_w, H = p->g.det_h;
+  const size_t tile = (size_t)p->P_pad * (TF / 2 + 1) * 4;
+  const size_t tabs = ((size_t)W + H + (size_t)p->g.pw * p->g.ph) * 2;
+  // binning tables in shared memory when they fit beside the tile (a raw-pixel
+  // table in global memory otherwise, or the three global tables without it)
+  const int tab_smem = tabs <= kScatterTabBytes;
+  const size_t sm = tile + (tab_smem ? (tabs + 15) / 16 * 16 : 0);
   cudaError_t e = ensure_smem((const void*)k_scatter, sm);
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;
   const uint64_t tiles = (first + n - T0 + TF - 1) / TF;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, kThreads, sm);
+  uint64_t grid = (uint64_t)nsm * (occ > 0 ? occ : 1);
+  if (grid > tiles) grid = tiles;
   stage_begin(p, EER4D_STAGE_SCATTER, s);
-  k_scatter<<<(unsigned)tiles, kThreads, sm, s>>>(
-      idx, n_idx, off, first, n, p->g.det_w * p->g.det_h, p->dw, p->d_lutp, p->d_lutx, p->d_luty,
-      p->d_lut2,
-      (int)p->g.pw, p->P_pad, TF, (uint64_t)p->F, counts, st);
+  k_scatter<<<(unsigned)grid, kThreads, sm, s>>>(
+      idx, n_idx, off, first, n, W, H, p->dw, p->d_lutp, p->d_lutx, p->d_luty, p->d_lut2,
+      (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, tiles, tab_smem, (uint64_t)p->cstride, counts, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_SCATTER, s);
   return cudaGetLastError();
