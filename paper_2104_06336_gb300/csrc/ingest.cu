@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict_
 // global memory.
 constexpr int kMaxFrameEvents = 65535;
 
-__global__ void __launch_bounds__(kThreads, 2) k_scatter(
+#ifndef EER4D_SCATTER_MINB
+#define EER4D_SCATTER_MINB 2
+#endif
+__global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     const uint32_t* __restrict__ idx, uint64_t n_idx, const uint64_t* __restrict__ off,
     uint64_t first, uint64_t nfr, uint32_t W, uint32_t H, DivMod dw,
     const int16_t* __restrict__ lutp, const int16_t* __restrict__ lutx,
