@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--refocus-steps", type=int, default=220)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch shapes instead of timing the candidates first")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the comparison of the scan-DFT forms (fused FP32, plain Stockham, split-FP16)")
     ap.add_argument("--batching", action="store_true",
                     help="also time the 16-dataset batching workload: one batched launch vs one call per dataset")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split"],
@@ -228,6 +232,7 @@ def run_ours(args, rank, world, local_rank):
     C, F = idx.numel(), w.n_frames
     prec = P.SPLIT_FP16 if args.precision == "split" else P.FP32_FFT
     rec = P.Reconstructor(geom, precision=prec, n_cand=64, device=dev)
+    tuned = P.tuning.autotune(rec, idx, off) if not args.no_autotune else None
     Ny, nkx, P_pad = w.scan_ny, rec.info["nkx"], rec.info["P_pad"]
     theta = torch.zeros(5, dtype=torch.float64, device=dev)
     sums = torch.empty(3, F, dtype=torch.int64, device=dev)
@@ -314,12 +319,49 @@ def run_ours(args, rank, world, local_rank):
                          (4 * C / 1e6, 8 * P_pad * Ny * nkx / 1e9),
                    "parallelism": f"replicas x{world} (independent datasets, no collective)"},
         "gpu_launches": launches,
+        "tuning": tuned,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(ach / hbm, 3), "traffic": traffic,
                      "peak_source": hsrc, "algorithmic_bytes": sb[dom]},
         "stages": stages,
         "clocks": clk.summary(),
     }
+
+    # ---- the scan-DFT forms on the same events ----------------------------
+    # fused FP32 register FFT (one persistent launch), the plain FP32 Stockham
+    # form (two launches + transpose) and the split-FP16 tcgen05 DFT along x:
+    # ssb_accumulate time and the phase against the fused form's
+    if not args.no_forms:
+        ref_ph = torch.empty(1, Ny, w.scan_nx, dtype=torch.float32, device=dev)
+        v1 = torch.empty(1, dtype=torch.float64, device=dev)
+        forms = {}
+        for name, prec_f in (("fp32_fused", P.FP32_FFT), ("fp32_stockham", P.FP32_STOCKHAM),
+                             ("split_fp16_tcgen05", P.SPLIT_FP16)):
+            rf = P.Reconstructor(geom, precision=prec_f, device=dev)
+            rf.totals.zero_()
+
+            def acc():
+                P.ssb_accumulate(rf.plan, idx, off, 0, rf.work, rf.G, True, status=rf.status)
+
+            acc()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                acc()
+            b.record()
+            torch.cuda.synchronize()
+            ph_f = torch.empty(1, Ny, w.scan_nx, dtype=torch.float32, device=dev)
+            P.ssb_reconstruct(rf.plan, rf.G, theta, rf.scratch, ph_f, v1, status=rf.status)
+            torch.cuda.synchronize()
+            rf.check()
+            if name == "fp32_fused":
+                ref_ph.copy_(ph_f)
+            err = float((ph_f - ref_ph).double().norm() / ref_ph.double().norm())
+            forms[name] = {"accumulate_ms": a.elapsed_time(b) / 3, "phase_rel_l2_vs_fused": err}
+            del rf
+            torch.cuda.empty_cache()
+        out["dft_forms"] = forms
 
     # ---- end to end through the public API with host buffers -------------
     if not args.no_e2e:

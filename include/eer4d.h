@@ -63,6 +63,9 @@ extern "C" {
 #define EER4D_FP32_FFT_2PASS 2  /* FP32 radix FFT, always as two launches (x per chunk,
                                    y at the end) through a full-size intermediate; the
                                    same arithmetic as EER4D_FP32_FFT */
+#define EER4D_FP32_STOCKHAM 3   /* the plain form: FP32 shared-memory Stockham FFT
+                                   (radix 8/4/2 and odd primes) for both axes, two
+                                   launches plus a transpose */
 #define EER4D_NORM_NONE  0  /* Eq. 3 as printed: S(K) = sum over K(K) */
 #define EER4D_NORM_AREA  1  /* S(K) / |K(K)| (0 when the set is empty) */
 
@@ -109,7 +112,8 @@ typedef struct eer4d_plan eer4d_plan;
 
 /* ---- plan ---------------------------------------------------------------- */
 /* Validates the geometry, builds the pixel, row and FFT tables on the current
- * device.  precision: EER4D_FP32_FFT, EER4D_SPLIT_FP16 or EER4D_FP32_FFT_2PASS; norm:
+ * device.  precision: EER4D_FP32_FFT, EER4D_SPLIT_FP16, EER4D_FP32_FFT_2PASS or
+ * EER4D_FP32_STOCKHAM; norm:
  * EER4D_NORM_NONE or EER4D_NORM_AREA.  Returns EINVAL for an invalid
  * geometry (zero sizes, odd scan, crop_px < k0_px, more than 32767 kept
  * pixels, scan side > 4096), ENOMEM/ECUDA when the tables cannot be made. */
@@ -314,6 +318,37 @@ int ssb_reconstruct_batched(const eer4d_plan* const* h_plans, const void* const*
 #define EER4D_STATIC_SCRATCH_BYTES (8u << 20)
 int ssb_reconstruct_static(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
                            float* d_phase, double* d_var, uint32_t* d_status, void* stream);
+
+/* ---- launch-shape autotuner (not part of the method) --------------------------
+ * Tile and grid shapes of the three main kernels.  Zero means the built-in
+ * choice.  scatter_tf: frames per scatter tile (a power of two, 4..128);
+ * *_ctas_per_sm: resident CTAs per SM of the persistent grids of the scatter,
+ * the fused scan DFT and the trotter kernel (capped by occupancy).  ms: the
+ * times (ms) the autotuner measured for its choices (scatter, DFT, trotter). */
+typedef struct eer4d_tuning {
+  int32_t scatter_tf;
+  int32_t scatter_ctas_per_sm;
+  int32_t dft_ctas_per_sm;
+  int32_t trotter_ctas_per_sm;
+  float   ms[3];
+} eer4d_tuning;
+/* Times the candidate shapes on the caller's data and keeps the fastest in the
+ * plan: scatter (every tile size that fits shared memory x 1..3 CTAs/SM) over
+ * the whole CSR (d_idx, d_off for all scan_ny*scan_nx frames), the fused scan
+ * DFT (1..4 CTAs/SM; plans without it keep 0) and the trotter kernel with the
+ * aberrations d_aberr (double[5]) (1..3 CTAs/SM).  d_work, d_G and d_scratch
+ * are the buffers of eer4d_workspace_bytes (n_cand >= 1); they are
+ * overwritten.  Synchronises `stream` (a set-up call: not for stream
+ * capture).  The choice is written to *h_out (nullable).  Results of every
+ * call are unchanged by the choice except the summation order of the adjoint's
+ * per-block partial sums. */
+int eer4d_autotune(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                   void* d_work, void* d_G, void* d_scratch, const double* d_aberr,
+                   uint32_t* d_status, void* stream, eer4d_tuning* h_out);
+/* Applies a stored choice (for example from a cache of earlier eer4d_autotune
+ * results) without timing; EINVAL for values out of range. */
+int eer4d_set_tuning(eer4d_plan* plan, const eer4d_tuning* h_tuning);
+int eer4d_get_tuning(const eer4d_plan* plan, eer4d_tuning* h_tuning);
 
 /* ---- measurement hooks (not part of the method) ------------------------------
  * Stage ids for eer4d_set_stage_events. */

@@ -8,13 +8,15 @@ from . import _lib
 from ._lib import (  # noqa: F401  (C-ABI names)
     Plan, Eer4dError, eer_load_csr, com_dpc, ssb_accumulate, ssb_reconstruct, ssb_grad,
     ssb_variance_grad, ssb_trotter_counts, ssb_refocus_step, eer4d_set_stage_events,
-    eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, NORM_NONE, NORM_AREA,
+    eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, FP32_STOCKHAM, NORM_NONE, NORM_AREA,
     ssb_reconstruct_batched, batched_scratch_bytes, MAX_SETS, eer_decode_rle,
-    virtual_detectors, MAX_RINGS, ssb_g_slices, MAX_SLICES, dpc_iterative,
+    virtual_detectors, MAX_RINGS, ssb_g_slices, MAX_SLICES, dpc_iterative, eer4d_autotune,
+    eer4d_set_tuning, eer4d_get_tuning,
 )
 from .pipeline import Reconstructor, reconstruct_batched  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401
 from . import refocus  # noqa: F401
+from . import tuning  # noqa: F401
 
 
 def build(force: bool = False) -> str:

@@ -20,7 +20,7 @@ EER4D_EOVERFLOW, EER4D_ETIMEOUT, EER4D_ECUDA, EER4D_ENOMEM, EER4D_EORDER = -4, -
 EER4D_ESCRATCH = -9
 STATIC_SCRATCH_BYTES = 8 << 20
 ST_RANGE, ST_OFFSETS, ST_OVERFLOW, ST_TIMEOUT, ST_ROTATION = 0x1, 0x2, 0x4, 0x8, 0x10
-FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS = 0, 1, 2
+FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, FP32_STOCKHAM = 0, 1, 2, 3
 NORM_NONE, NORM_AREA = 0, 1
 
 EXPORTS = [
@@ -29,7 +29,8 @@ EXPORTS = [
     "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
     "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
-    "virtual_detectors", "ssb_g_slices", "dpc_iterative",
+    "virtual_detectors", "ssb_g_slices", "dpc_iterative", "eer4d_autotune", "eer4d_set_tuning",
+    "eer4d_get_tuning",
 ]
 MAX_SLICES = 64
 MAX_RINGS = 64
@@ -48,6 +49,28 @@ class Geom(C.Structure):
         ("lambda_A", C.c_double), ("dalpha_rad", C.c_double), ("step_A", C.c_double),
         ("dalpha_raw_rad", C.c_double),
     ]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("scatter_tf", C.c_int32), ("scatter_ctas_per_sm", C.c_int32),
+                ("dft_ctas_per_sm", C.c_int32), ("trotter_ctas_per_sm", C.c_int32),
+                ("ms", C.c_float * 3)]
+
+    def as_dict(self) -> dict:
+        return {"scatter_tf": self.scatter_tf, "scatter_ctas_per_sm": self.scatter_ctas_per_sm,
+                "dft_ctas_per_sm": self.dft_ctas_per_sm,
+                "trotter_ctas_per_sm": self.trotter_ctas_per_sm, "ms": list(self.ms)}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Tuning":
+        t = cls()
+        t.scatter_tf = int(d.get("scatter_tf", 0))
+        t.scatter_ctas_per_sm = int(d.get("scatter_ctas_per_sm", 0))
+        t.dft_ctas_per_sm = int(d.get("dft_ctas_per_sm", 0))
+        t.trotter_ctas_per_sm = int(d.get("trotter_ctas_per_sm", 0))
+        for i, v in enumerate(list(d.get("ms", [0, 0, 0]))[:3]):
+            t.ms[i] = float(v)
+        return t
 
 
 class Info(C.Structure):
@@ -101,6 +124,9 @@ def load(path: str | None = None):
         "ssb_reconstruct_batched": (I32, [P, P, I32, P, P, P, P, P, P]),
         "eer_decode_rle": (I32, [P, U64, P, U64, P, P, P]),
         "dpc_iterative": (I32, [P, P, D, D, D, I32, I32, P, S, P, P]),
+        "eer4d_autotune": (I32, [P, P, U64, P, P, P, P, P, P, P, C.POINTER(Tuning)]),
+        "eer4d_set_tuning": (I32, [P, C.POINTER(Tuning)]),
+        "eer4d_get_tuning": (I32, [P, C.POINTER(Tuning)]),
         "ssb_g_slices": (I32, [P, P, C.POINTER(C.c_int32), I32, P, P]),
         "virtual_detectors": (I32, [P, P, U64, P, U64, C.POINTER(D), I32, P, D, D, P, P, P, P]),
     }
@@ -326,3 +352,25 @@ def dpc_iterative(plan: Plan, com, phase, scratch, n_iter: int, mu: float = 0.5,
                                 int(n_iter), int(pad), _ptr(scratch, "scratch"),
                                 scratch.numel() * scratch.element_size(), _ptr(phase, "phase"),
                                 _stream()), "dpc_iterative")
+
+
+def eer4d_autotune(plan: Plan, idx, off, work, G, scratch, aberr, status=None) -> dict:
+    """Times the launch-shape candidates on this data and keeps the fastest in
+    the plan (synchronises the current stream).  Returns the choice."""
+    t = Tuning()
+    _check(load().eer4d_autotune(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                                 _ptr(work, "work"), _ptr(G, "G"), _ptr(scratch, "scratch"),
+                                 _ptr(aberr, "aberr"), _ptr(status, "status"), _stream(),
+                                 C.byref(t)), "eer4d_autotune")
+    return t.as_dict()
+
+
+def eer4d_set_tuning(plan: Plan, tuning: dict):
+    t = Tuning.from_dict(tuning)
+    _check(load().eer4d_set_tuning(plan.handle, C.byref(t)), "eer4d_set_tuning")
+
+
+def eer4d_get_tuning(plan: Plan) -> dict:
+    t = Tuning()
+    _check(load().eer4d_get_tuning(plan.handle, C.byref(t)), "eer4d_get_tuning")
+    return t.as_dict()

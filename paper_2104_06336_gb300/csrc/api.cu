@@ -151,7 +151,7 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   *out = nullptr;
   if (!geom_ok(h_geom)) return EER4D_EINVAL;
   if (precision != EER4D_FP32_FFT && precision != EER4D_SPLIT_FP16 &&
-      precision != EER4D_FP32_FFT_2PASS)
+      precision != EER4D_FP32_FFT_2PASS && precision != EER4D_FP32_STOCKHAM)
     return EER4D_EINVAL;
   if (norm != EER4D_NORM_NONE && norm != EER4D_NORM_AREA) return EER4D_EINVAL;
   const eer4d_geom& g = *h_geom;
@@ -504,6 +504,144 @@ int ssb_g_slices(const eer4d_plan* p, const void* d_G, const int32_t* h_bins, in
       return EER4D_EINVAL;
   return cuda_fail(launch_g_slices(p, static_cast<const float2*>(d_G), h_bins, n,
                                    static_cast<float2*>(d_out), (cudaStream_t)stream));
+}
+
+// ---- launch-shape autotuner ------------------------------------------------
+static bool tuning_ok(const eer4d_tuning* t) {
+  const int tf = t->scatter_tf;
+  if (tf != 0 && (tf < 4 || tf > 128 || (tf & (tf - 1)))) return false;
+  return t->scatter_ctas_per_sm >= 0 && t->scatter_ctas_per_sm <= 32 && t->dft_ctas_per_sm >= 0 &&
+         t->dft_ctas_per_sm <= 32 && t->trotter_ctas_per_sm >= 0 && t->trotter_ctas_per_sm <= 32;
+}
+
+int eer4d_set_tuning(eer4d_plan* p, const eer4d_tuning* t) {
+  if (!p || !t || !tuning_ok(t)) return EER4D_EINVAL;
+  p->tune = *t;
+  return EER4D_OK;
+}
+
+int eer4d_get_tuning(const eer4d_plan* p, eer4d_tuning* t) {
+  if (!p || !t) return EER4D_EINVAL;
+  *t = p->tune;
+  return EER4D_OK;
+}
+
+extern "C++" {
+namespace {
+// mean time of `reps` runs of fn after one untimed run; negative on a failure
+template <typename Fn>
+float time_ms(cudaStream_t s, int reps, Fn fn) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1.f; }
+  float ms = -1.f;
+  if (fn() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = fn() == cudaSuccess;
+    if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+      ms /= reps;
+    else
+      ms = -1.f;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+}  // namespace
+}  // extern "C++"
+
+int eer4d_autotune(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                   void* d_work, void* d_G, void* d_scratch, const double* d_aberr,
+                   uint32_t* d_status, void* stream, eer4d_tuning* h_out) {
+  if (!p || !d_off || (n_idx && !d_idx) || !d_work || !d_G || !d_scratch || !d_aberr)
+    return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the caller's stage events stay out of the timing runs
+  cudaEvent_t save_a[EER4D_N_STAGES], save_b[EER4D_N_STAGES];
+  for (int i = 0; i < EER4D_N_STAGES; ++i) {
+    save_a[i] = p->ev_start[i];
+    save_b[i] = p->ev_stop[i];
+    p->ev_start[i] = p->ev_stop[i] = nullptr;
+  }
+  __half* counts = static_cast<__half*>(d_work);
+  float2* X1 = reinterpret_cast<float2*>(static_cast<unsigned char*>(d_work) +
+                                         al256(work_counts_bytes(p)));
+  float2* G = static_cast<float2*>(d_G);
+  const eer4d_tuning keep = p->tune;
+  eer4d_tuning best = keep;
+  int rc = EER4D_OK;
+  // scatter: tile sizes that fit shared memory x 1..3 resident CTAs per SM
+  {
+    float tbest = -1.f;
+    for (int tf = 16; tf <= 128; tf *= 2) {
+      const size_t tile = (size_t)p->P_pad * (tf / 2 + 1) * 4;
+      if (tile > 160 * 1024) continue;
+      for (int cps = 1; cps <= 3; ++cps) {
+        p->tune = best;
+        p->tune.scatter_tf = tf;
+        p->tune.scatter_ctas_per_sm = cps;
+        const float ms = time_ms(s, 2, [&] {
+          return launch_scatter(p, d_idx, n_idx, d_off, 0, (uint64_t)p->F, counts, d_status, s);
+        });
+        if (ms > 0.f && (tbest < 0.f || ms < tbest)) {
+          tbest = ms;
+          best.scatter_tf = tf;
+          best.scatter_ctas_per_sm = cps;
+        }
+      }
+    }
+    best.ms[0] = tbest;
+    p->tune = best;
+    // counts of the chosen shape for the DFT runs below
+    rc = cuda_fail(launch_scatter(p, d_idx, n_idx, d_off, 0, (uint64_t)p->F, counts, d_status, s));
+  }
+  // fused scan DFT: 1..4 CTAs per SM
+  if (rc == EER4D_OK && dft2_fused_ok(p)) {
+    unsigned* ctl = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(X1) +
+                                                al256(dft2_ring_bytes(p)));
+    float tbest = -1.f;
+    for (int cps = 1; cps <= 4; ++cps) {
+      p->tune = best;
+      p->tune.dft_ctas_per_sm = cps;
+      const float ms = time_ms(s, 2, [&] { return launch_dft2_fused(p, counts, X1, G, ctl, d_status, s); });
+      if (ms > 0.f && (tbest < 0.f || ms < tbest)) {
+        tbest = ms;
+        best.dft_ctas_per_sm = cps;
+      }
+    }
+    best.ms[1] = tbest;
+    p->tune = best;
+    rc = cuda_fail(launch_dft2_fused(p, counts, X1, G, ctl, d_status, s));
+  } else if (rc == EER4D_OK) {
+    rc = cuda_fail(launch_stage1(p, counts, X1, 0, (int)p->g.scan_ny, s));
+    if (rc == EER4D_OK) rc = cuda_fail(launch_stage2(p, X1, G, s));
+  }
+  // trotter: 1..3 CTAs per SM, one candidate
+  if (rc == EER4D_OK) {
+    float tbest = -1.f;
+    for (int cps = 1; cps <= 3; ++cps) {
+      p->tune = best;
+      p->tune.trotter_ctas_per_sm = cps;
+      const float ms = time_ms(s, 2, [&] {
+        return launch_trotter(p, G, d_aberr, 1, TROT_FWD, d_scratch, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, d_status, s);
+      });
+      if (ms > 0.f && (tbest < 0.f || ms < tbest)) {
+        tbest = ms;
+        best.trotter_ctas_per_sm = cps;
+      }
+    }
+    best.ms[2] = tbest;
+  }
+  p->tune = rc == EER4D_OK ? best : keep;
+  for (int i = 0; i < EER4D_N_STAGES; ++i) {
+    p->ev_start[i] = save_a[i];
+    p->ev_stop[i] = save_b[i];
+  }
+  if (rc == EER4D_OK) rc = cuda_fail(cudaStreamSynchronize(s));
+  if (h_out) *h_out = p->tune;
+  return rc;
 }
 
 int ssb_trotter_counts(const eer4d_plan* p, const double* d_aberr, int32_t* d_count,

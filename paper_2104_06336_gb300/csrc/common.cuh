@@ -75,6 +75,8 @@ struct eer4d_plan {
   FftDesc fy, fx, fy2, fx2;
   // streaming state of ssb_accumulate (host)
   uint64_t next_frame;
+  // launch shapes chosen by eer4d_autotune / eer4d_set_tuning (0 = built-in choice)
+  eer4d_tuning tune;
   // optional per-stage timing events (caller-owned cudaEvent_t), see
   // eer4d_set_stage_events
   cudaEvent_t ev_start[EER4D_N_STAGES];
@@ -141,6 +143,7 @@ cudaError_t launch_virtual_detectors(const eer4d_plan* p, const uint32_t* idx, u
                                      void* scratch, int32_t* out, uint32_t* st, cudaStream_t s);
 cudaError_t launch_rle_decode(const uint32_t* runs, uint64_t n, const uint64_t* off,
                               uint64_t n_frames, uint32_t* idx, uint32_t* st, cudaStream_t s);
+int scatter_tf_for(const eer4d_plan* p);
 cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                            const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
                            uint32_t* st, cudaStream_t s);

@@ -216,7 +216,9 @@ cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, fl
   q.total = (long long)q.n_groups * (q.n1 + q.n2);
   q.F = p->cstride;
   if ((e = cudaMemsetAsync(ctl, 0, ctl_bytes, s)) != cudaSuccess) return e;
-  long long grid = (long long)(per_sm > 0 ? per_sm : 1) * nsm;
+  int cps = per_sm > 0 ? per_sm : 1;
+  if (p->tune.dft_ctas_per_sm > 0 && p->tune.dft_ctas_per_sm < cps) cps = p->tune.dft_ctas_per_sm;
+  long long grid = (long long)cps * nsm;
   if (grid > q.total) grid = q.total;
   k_dft2_fused<R1, R2, CP><<<(unsigned)grid, NT, sm, s>>>(counts, ring, G, p->fx.tw, p->fy.tw, q,
                                                           ctl, st);

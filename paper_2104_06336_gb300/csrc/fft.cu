@@ -314,7 +314,7 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
   if (y1 <= y0) return cudaSuccess;
   const FftDesc& d = p->fx;
   const long long NRl = p->cstride;
-  if (reg_size(d.N)) {
+  if (reg_size(d.N) && p->precision != EER4D_FP32_STOCKHAM) {
     stage_begin(p, EER4D_STAGE_DFT_X, s);
     cudaError_t e = r2c_reg(d, counts, G, p->P_pad, y0, y1 - y0, NRl, (long long)p->g.scan_nx,
                             (long long)p->g.scan_ny * p->P_pad, 1, (long long)p->P_pad, s);
@@ -342,7 +342,7 @@ cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cuda
   const long long bs = (long long)Ny * p->P_pad;
   stage_begin(p, EER4D_STAGE_DFT_Y, s);
   cudaError_t e;
-  if (reg_size(p->fy.N)) {
+  if (reg_size(p->fy.N) && p->precision != EER4D_FP32_STOCKHAM) {
     e = cols_reg<1, true>(p->fy, X1, G, p->P_pad, p->P_pad, Ny, bs, bs, p->nkx, 1.f, s);
   } else {
     // generic lengths: in-place column FFT, then a tiled transpose into G

@@ -396,11 +396,15 @@ cudaError_t launch_com(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
   return cudaGetLastError();
 }
 
+int scatter_tf_for(const eer4d_plan* p) {
+  return p->tune.scatter_tf > 0 ? p->tune.scatter_tf : scatter_tf(p->P_pad);
+}
+
 cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                            const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
                            uint32_t* st, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int TF = scatter_tf(p->P_pad);
+  const int TF = scatter_tf_for(p);
   const uint32_t W = p->g.det_w, H = p->g.det_h;
   const size_t tile = (size_t)p->P_pad * (TF / 2 + 1) * 4;
   const size_t tabs = ((size_t)W + H + (size_t)p->g.pw * p->g.ph) * 2;
@@ -416,7 +420,10 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, kThreads, sm);
-  uint64_t grid = (uint64_t)nsm * (occ > 0 ? occ : 1);
+  if (occ < 1) return cudaErrorInvalidConfiguration;  // the tile does not fit shared memory
+  const int cps = p->tune.scatter_ctas_per_sm > 0 && p->tune.scatter_ctas_per_sm < occ
+                      ? p->tune.scatter_ctas_per_sm : occ;
+  uint64_t grid = (uint64_t)nsm * cps;
   if (grid > tiles) grid = tiles;
   stage_begin(p, EER4D_STAGE_SCATTER, s);
   k_scatter<<<(unsigned)grid, kThreads, sm, s>>>(

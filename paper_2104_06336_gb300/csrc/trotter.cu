@@ -610,7 +610,10 @@ int trot_blocks(const eer4d_plan* p, const void* kern, size_t smem) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
-  int b = nsm * (occ > 0 ? occ : 1);
+  int cps = occ > 0 ? occ : 1;
+  if (p->tune.trotter_ctas_per_sm > 0 && p->tune.trotter_ctas_per_sm < cps)
+    cps = p->tune.trotter_ctas_per_sm;
+  int b = nsm * cps;
   if (b > need) b = need;
   if (b > kMaxTrotBlocks) b = kMaxTrotBlocks;
   return b < 1 ? 1 : b;

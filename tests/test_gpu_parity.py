@@ -342,6 +342,19 @@ def test_fused_dft_256_matches_oracle_and_two_pass(c2full):
     assert torch.equal(_two_pass_G(c2full).G, c2full.rec.G)
 
 
+def test_stockham_form_matches_fused(c2full):
+    """The plain FP32 Stockham form (two launches and a transpose) against the
+    fused register FFT on the 256x256 precision workload: G within 2e-6 of
+    max|G|."""
+    import paper_2104_06336_gb300 as P
+    rec = P.Reconstructor(c2full.geom, precision=P.FP32_STOCKHAM)
+    rec.load(c2full.idx, c2full.off)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    a, b = rec.G_complex(), c2full.rec.G_complex()
+    assert float((a - b).abs().max()) <= 2e-6 * float(b.abs().max())
+
+
 @pytest.mark.parametrize("n", [128, 512])
 def test_fused_dft_other_sizes_match_two_pass(n):
     """The 128 (groups of 16 pixels) and 512 (groups of 8) instantiations
@@ -491,6 +504,36 @@ def test_rle_decode_flags_overflow_and_bad_offsets():
     P.eer_decode_rle(runs, bad, status=st)
     torch.cuda.synchronize()
     assert P.status_code(st) == P._lib.EER4D_EOFFSETS
+
+
+# ------------------------------------------------ launch-shape autotuner ----
+@pytest.mark.parametrize("n", [0, 128])
+def test_autotune_keeps_results_and_caches(n, c2small, tmp_path):
+    """The autotuner's choice changes no result: counts, G and the phase are
+    bit-identical to the built-in shapes; a cached choice is applied without
+    timing; out-of-range shapes are rejected."""
+    import paper_2104_06336_gb300 as P
+    c = c2small if n == 0 else Case(synth.workload(2, scan_ny=n, scan_nx=n), device_gen="cuda")
+    rec = P.Reconstructor(c.geom)
+    cache = str(tmp_path / "tune.json")
+    t = P.tuning.autotune(rec, c.idx, c.off, cache=cache)
+    assert t["scatter_tf"] in (16, 32, 64, 128) and 1 <= t["scatter_ctas_per_sm"] <= 3
+    assert 1 <= t["trotter_ctas_per_sm"] <= 3
+    assert (t["dft_ctas_per_sm"] == 0) == (n == 0)
+    assert all(m > 0 for m, k in zip(t["ms"], (1, n, 1)) if k)
+    rec.load(c.idx, c.off)
+    ph, var = rec.reconstruct(torch.tensor([40.0, 5.0, -5.0, 0.0, 0.0], dtype=torch.float64))
+    ph0, var0 = c.rec.reconstruct(torch.tensor([40.0, 5.0, -5.0, 0.0, 0.0], dtype=torch.float64))
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    assert torch.equal(rec.counts, c.rec.counts)
+    assert torch.equal(rec.G, c.rec.G)
+    assert torch.equal(ph, ph0)
+    rec2 = P.Reconstructor(c.geom)
+    assert P.tuning.autotune(rec2, c.idx, c.off, cache=cache) == t
+    assert P.eer4d_get_tuning(rec2.plan)["scatter_tf"] == t["scatter_tf"]
+    with pytest.raises(P.Eer4dError):
+        P.eer4d_set_tuning(rec2.plan, dict(t, scatter_tf=48))
 
 
 # ------------------------------------------ uneven batches, one launch ------
