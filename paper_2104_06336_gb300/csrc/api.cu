@@ -89,6 +89,9 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_pix);
   cudaFree(p->d_bfp);
   cudaFree(p->d_rows);
+  cudaFree(p->d_tl_mask);
+  cudaFree(p->d_tl_q);
+  cudaFree(p->d_tl_n);
   cudaFree(p->d_tw_y);
   cudaFree(p->d_tw_x);
   cudaFree(p->d_tw_y2);
@@ -99,6 +102,8 @@ void free_plan(eer4d_plan* p) {
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t kTrotterListsMaxBytes = (size_t)512 << 20;
 
 }  // namespace
 
@@ -250,6 +255,16 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
     const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
     free_plan(p);
     return rc;
+  }
+  // trotter membership lists at rotation 0 when they are small enough to keep
+  if (trotter_lists_bytes(p) <= kTrotterListsMaxBytes && build_trotter_lists(p) != cudaSuccess) {
+    cudaGetLastError();  // lists are optional: without them the kernel evaluates the masks
+    cudaFree(p->d_tl_mask);
+    cudaFree(p->d_tl_q);
+    cudaFree(p->d_tl_n);
+    p->d_tl_mask = nullptr;
+    p->d_tl_q = nullptr;
+    p->d_tl_n = nullptr;
   }
   if (precision == EER4D_SPLIT_FP16 && (e = make_dftx_tc(p)) != cudaSuccess) {
     const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);

@@ -68,6 +68,10 @@ struct eer4d_plan {
   __half* d_dft_hi;          // split-FP16 DFT matrix along x (tile-blocked), SPLIT_FP16 plans
   __half* d_dft_lo;
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
+  uint2* d_tl_mask;          // trotter membership lists at rotation 0 (NULL: none)
+  uint16_t* d_tl_q;
+  int* d_tl_n;
+  int tl_cap;
   float2* d_tw_y;            // [scan_ny]
   float2* d_tw_x;            // [scan_nx]
   float2* d_tw_y2;           // [2 scan_ny] (zero-padded DPC grid)
@@ -182,6 +186,8 @@ cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cud
 enum { TROT_FWD = 0, TROT_GRAD = 1, TROT_VARGRAD = 2, TROT_COUNT = 3 };
 cudaError_t launch_ascent(double* theta, const double* step, const double* grad, cudaStream_t s);
 size_t trotter_batched_scratch_bytes(const eer4d_plan* const* plans, int n);
+size_t trotter_lists_bytes(const eer4d_plan* p);
+cudaError_t build_trotter_lists(eer4d_plan* p);
 cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2* const* G, int n,
                                    const double* aberr, void* scratch, float* const* phase,
                                    double* var, uint32_t* st, cudaStream_t s);

@@ -129,6 +129,24 @@ __device__ __forceinline__ float dist2(float kx, float ky, float Kx, float Ky) {
   return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
 }
 
+// Membership of detector pixel kk in the bin's two sets (the exact float32
+// rule): memP for K(K'(b)), memM for K(K'(-b)); off Nyquist K'(-b) = -K'(b)
+// and the two distances serve both sets.
+__device__ __forceinline__ void member_bits(float2 kk, float Kpx, float Kpy, float Kmx, float Kmy,
+                                            bool nyq, bool active, float k0sq, bool& memP,
+                                            bool& memM) {
+  const float dm = dist2(kk.x, kk.y, Kpx, Kpy);
+  const float dp = dist2(kk.x, kk.y, -Kpx, -Kpy);
+  memP = active && dm < k0sq && dp > k0sq;
+  if (!nyq) {
+    memM = active && dp < k0sq && dm > k0sq;
+  } else {
+    const float em = dist2(kk.x, kk.y, Kmx, Kmy);
+    const float ep = dist2(kk.x, kk.y, -Kmx, -Kmy);
+    memM = active && em < k0sq && ep > k0sq;
+  }
+}
+
 __device__ __forceinline__ float2 cmadd(float2 acc, float2 a, float w) {
   return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
 }
@@ -151,7 +169,9 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TRO
     k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
               const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
-              const float2* __restrict__ W, float2* H, double* partial, int32_t* count) {
+              const float2* __restrict__ W, float2* H, double* partial, int32_t* count,
+              const uint2* __restrict__ tl_mask, const uint16_t* __restrict__ tl_q,
+              const int* __restrict__ tl_n, int tl_cap) {
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
   extern __shared__ unsigned char smem_raw[];
   float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
@@ -167,6 +187,8 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TRO
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const CandCoef c0 = coef[0];
+  // the plan's membership lists hold the sets at scan rotation 0
+  const bool lists = tl_n != nullptr && c0.c == 1.f && c0.s == 0.f;
   const float scale = MODE == TROT_COUNT ? 0.f : (float)gscale[1];
   const int nyw = (P.Ny + 31) >> 5;
   const int ntask = P.nkx * nyw;
@@ -254,43 +276,23 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TRO
         }
       };
 
-      // Pixels in batches of kBatch: memberships first, then every member's G
-      // load issued before any is used (kBatch loads in flight per lane).
-      for (int q0 = 0; q0 < P.P_bf; q0 += kBatch) {
-        unsigned mP = 0u, mM = 0u;
-#pragma unroll
-        for (int i = 0; i < kBatch; ++i) {
-          const int q = q0 + i;
-          if (q >= P.P_bf) break;
-          const float2 kk = skk[q];
-          const float dm = dist2(kk.x, kk.y, Kpx, Kpy);
-          const float dp = dist2(kk.x, kk.y, -Kpx, -Kpy);
-          const bool memP = active && dm < P.k0sq && dp > P.k0sq;
-          bool memM;
-          if (!nyq) {
-            memM = active && dp < P.k0sq && dm > P.k0sq;
-          } else {
-            const float em = dist2(kk.x, kk.y, Kmx, Kmy);
-            const float ep = dist2(kk.x, kk.y, -Kmx, -Kmy);
-            memM = active && em < P.k0sq && ep > P.k0sq;
-          }
-          mP |= (unsigned)memP << i;
-          mM |= (unsigned)memM << i;
-        }
+      // A batch of kBatch pixels q[i] with this lane's membership bits: every
+      // member's G load is issued before any is used (kBatch loads in flight).
+      auto batch = [&](unsigned mP, unsigned mM, const int (&qv)[kBatch]) {
         nP += __popc(mP);
         nM += __popc(mM);
-        if (MODE == TROT_COUNT) continue;
+        if (MODE == TROT_COUNT) return;
         const unsigned mAny = mP | mM;
-        if (mAny == 0u) continue;
+        if (mAny == 0u) return;
         float2 gb[kBatch];
 #pragma unroll
         for (int i = 0; i < kBatch; ++i)
-          gb[i] = ((mAny >> i) & 1u) ? Gl[(size_t)sp[q0 + i] * P.Ny] : make_float2(0.f, 0.f);
+          gb[i] = ((mAny >> i) & 1u) ? Gl[(size_t)sp[qv[i]] * P.Ny] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
           if (!(memP || memM)) continue;
-          const int q = q0 + i;
+          const int q = qv[i];
           const float2 kk = skk[q];
           const float2 g = gb[i];
           // Off Nyquist the two sets are disjoint, so one term per pixel: G into
@@ -303,6 +305,44 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TRO
             if (memP) contrib(g, Kpx, Kpy, kk, q, 1.f, SP, SM, DP, DM);
             if (memM) contrib(make_float2(g.x, -g.y), Kmx, Kmy, kk, q, 0.f, SP, SM, DP, DM);
           }
+        }
+      };
+      if (lists) {
+        // only the pixels with a member among the warp's bins, in ascending
+        // q, with the 32 lanes' bits (the same sums in the same order)
+        const int n = tl_n[t];
+        const uint2* mk = tl_mask + (size_t)t * tl_cap;
+        const uint16_t* qq = tl_q + (size_t)t * tl_cap;
+        for (int e0 = 0; e0 < n; e0 += kBatch) {
+          unsigned mP = 0u, mM = 0u;
+          int qv[kBatch];
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            qv[i] = 0;
+            if (e0 + i < n) {
+              const uint2 m = __ldg(mk + e0 + i);
+              qv[i] = __ldg(qq + e0 + i);
+              mP |= ((m.x >> lane) & 1u) << i;
+              mM |= ((m.y >> lane) & 1u) << i;
+            }
+          }
+          batch(mP, mM, qv);
+        }
+      } else {
+        for (int q0 = 0; q0 < P.P_bf; q0 += kBatch) {
+          unsigned mP = 0u, mM = 0u;
+          int qv[kBatch];
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const int q = q0 + i;
+            qv[i] = q < P.P_bf ? q : 0;
+            if (q >= P.P_bf) continue;
+            bool memP, memM;
+            member_bits(skk[q], Kpx, Kpy, Kmx, Kmy, nyq, active, P.k0sq, memP, memM);
+            mP |= (unsigned)memP << i;
+            mM |= (unsigned)memM << i;
+          }
+          batch(mP, mM, qv);
         }
       }
 
@@ -647,7 +687,8 @@ cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
   if (e != cudaSuccess) return e;
   *nblk = trot_blocks(p, kern, sm);
   k_trotter<MODE, NC><<<*nblk, kWarps * 32, sm, s>>>(tp, G, p->d_bfp, p->d_pix, coef, ek, gsc, W,
-                                                     H, partial, count);
+                                                     H, partial, count, p->d_tl_mask, p->d_tl_q,
+                                                     p->d_tl_n, p->tl_cap);
   return cudaGetLastError();
 }
 
@@ -830,4 +871,75 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
   }
   stage_end(p0, EER4D_STAGE_IMAGE, s);
   return cudaSuccess;
+}
+
+// ---- membership lists at scan rotation 0 (built once per plan) --------------
+// For every warp task (32 consecutive stored bins) the bright-field pixels with
+// a member among the task's bins, in ascending q, with two 32-bit masks (bit l
+// = bin my0 + l is a member of K(K'(b)) / K(K'(-b))), decided by the same
+// member_bits() the trotter kernel runs.  The trotter kernel then walks only
+// these pixels when the scan rotation is 0 (mask evaluation is about half of
+// its work).
+namespace {
+__global__ void __launch_bounds__(256) k_trot_lists(int Ny, int Nx, int nkx, int P_bf,
+                                                    float kpm_x, float kpm_y, float k0sq,
+                                                    const int32_t* __restrict__ bfp,
+                                                    const short2* __restrict__ pix, uint2* mask,
+                                                    uint16_t* qlist, int* nlist, int cap) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int nyw = (Ny + 31) >> 5;
+  if (t >= nkx * nyw) return;  // whole warp
+  CandCoef c0;
+  c0.c = 1.f;
+  c0.s = 0.f;
+  const int mx = t / nyw;
+  const int my0 = (t - mx * nyw) * 32;
+  const int my = my0 + lane;
+  const bool active = my < Ny;
+  const int mys = active ? my : 0;
+  const int mmx = (Nx - mx) % Nx, mmy = (Ny - mys) % Ny;
+  float Kpx, Kpy, Kmx, Kmy;
+  kprime(c0, kpm_x, kpm_y, freq_index(mx, Nx), freq_index(mys, Ny), Kpx, Kpy);
+  kprime(c0, kpm_x, kpm_y, freq_index(mmx, Nx), freq_index(mmy, Ny), Kmx, Kmy);
+  const bool nyq = (2 * mx == Nx) || (2 * mys == Ny);
+  int n = 0;
+  for (int q = 0; q < P_bf; ++q) {  // same trip count on every lane
+    const short2 k = pix[bfp[q]];
+    bool memP, memM;
+    member_bits(make_float2((float)k.x, (float)k.y), Kpx, Kpy, Kmx, Kmy, nyq, active, k0sq, memP,
+                memM);
+    const unsigned bp = __ballot_sync(0xffffffffu, memP);
+    const unsigned bm = __ballot_sync(0xffffffffu, memM);
+    if ((bp | bm) != 0u) {
+      if (lane == 0 && n < cap) {
+        mask[(size_t)t * cap + n] = make_uint2(bp, bm);
+        qlist[(size_t)t * cap + n] = (uint16_t)q;
+      }
+      ++n;
+    }
+  }
+  if (lane == 0) nlist[t] = n < cap ? n : cap;
+}
+}  // namespace
+
+size_t trotter_lists_bytes(const eer4d_plan* p) {
+  const size_t tasks = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
+  return tasks * (size_t)p->P_bf * (sizeof(uint2) + sizeof(uint16_t)) + tasks * sizeof(int);
+}
+
+cudaError_t build_trotter_lists(eer4d_plan* p) {
+  const size_t tasks = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
+  const int cap = p->P_bf;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_tl_mask, tasks * cap * sizeof(uint2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p->d_tl_q, tasks * cap * sizeof(uint16_t))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p->d_tl_n, tasks * sizeof(int))) != cudaSuccess) return e;
+  p->tl_cap = cap;
+  k_trot_lists<<<(unsigned)((tasks + 7) / 8), 256>>>(
+      (int)p->g.scan_ny, (int)p->g.scan_nx, p->nkx, p->P_bf, (float)p->g.kpm_x, (float)p->g.kpm_y,
+      (float)(p->g.k0_px * p->g.k0_px), p->d_bfp, p->d_pix, p->d_tl_mask, p->d_tl_q, p->d_tl_n,
+      cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaStreamSynchronize(0);
 }
