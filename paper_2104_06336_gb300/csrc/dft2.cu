@@ -234,7 +234,10 @@ bool dft2_fused_ok(const eer4d_plan* p) {
          (N == 128 || N == 256 || N == 512 || N == 1024);
 }
 
-static int dft2_gp(int N) { return N >= 512 ? 8 : 16; }
+#ifndef EER4D_DFT2_CP_LARGE
+#define EER4D_DFT2_CP_LARGE 4  // pixel pairs per S1 tile (= columns per S2 call) for N >= 512
+#endif
+static int dft2_gp(int N) { return N >= 512 ? 2 * EER4D_DFT2_CP_LARGE : 16; }
 
 size_t dft2_ring_bytes(const eer4d_plan* p) {
   const int N = (int)p->g.scan_nx;
@@ -252,8 +255,8 @@ cudaError_t launch_dft2_fused(const eer4d_plan* p, const __half* counts, float2*
   stage_begin(p, EER4D_STAGE_DFT_XY, s);
   cudaError_t e;
   switch (p->g.scan_nx) {
-    case 1024: e = launch_t<32, 32, 4>(p, counts, ring, G, ctl, cb, st, s); break;
-    case 512: e = launch_t<32, 16, 4>(p, counts, ring, G, ctl, cb, st, s); break;
+    case 1024: e = launch_t<32, 32, EER4D_DFT2_CP_LARGE>(p, counts, ring, G, ctl, cb, st, s); break;
+    case 512: e = launch_t<32, 16, EER4D_DFT2_CP_LARGE>(p, counts, ring, G, ctl, cb, st, s); break;
     case 256: e = launch_t<16, 16, 8>(p, counts, ring, G, ctl, cb, st, s); break;
     default: e = launch_t<16, 8, 8>(p, counts, ring, G, ctl, cb, st, s); break;
   }

@@ -165,7 +165,8 @@ __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, in
 // W = FFT(upstream gradient)), TROT_VARGRAD (V and dV/dtheta), TROT_COUNT
 // (|K(K)| per bin).
 template <int MODE, int NC>
-__global__ void __launch_bounds__(kWarps * 32, (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 3)
+__global__ void __launch_bounds__(kWarps * 32,
+                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : (NC > 1 ? 3 : 4))
     k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
               const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
