@@ -13,7 +13,7 @@ from ._lib import (  # noqa: F401  (C-ABI names)
     virtual_detectors, MAX_RINGS, ssb_g_slices, MAX_SLICES, dpc_iterative, eer4d_autotune,
     eer4d_set_tuning, eer4d_get_tuning,
 )
-from .pipeline import Reconstructor, reconstruct_batched  # noqa: F401
+from .pipeline import Reconstructor, reconstruct_batched, StreamedSteps  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401
 from . import refocus  # noqa: F401
 from . import tuning  # noqa: F401

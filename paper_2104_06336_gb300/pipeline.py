@@ -168,3 +168,50 @@ def reconstruct_batched(recs, aberr: torch.Tensor, phase: bool = True, scratch=N
     L.ssb_reconstruct_batched(plans, [r.G for r in recs], ab, scratch, ph, var,
                               status=recs[0].status)
     return ph, var
+
+
+class StreamedSteps:
+    """Double-buffered upload of each step's events, overlapped with the
+    previous step's computation.
+
+    ``run(h_idx, h_off, fn)`` copies the pinned host CSR (uint32 indices as an
+    int32 tensor, int64 offsets) into one of two device buffer pairs on a copy
+    stream, makes the current stream wait for that copy, calls
+    ``fn(d_idx, d_off)`` on the current stream (the whole path: library calls
+    and the device-to-host read of its results) and marks the buffer free when
+    the current stream has used it.  The next call's upload therefore runs on
+    the copy engine while this step computes; every step still uploads its own
+    events.  ``start(event)`` makes the next uploads wait for an event recorded
+    on the current stream (the start of a timed region)."""
+
+    def __init__(self, max_events: int, max_frames: int, device=None):
+        self.device = torch.device(device or "cuda")
+        self.bufs = [(torch.empty(max_events, dtype=torch.int32, device=self.device),
+                      torch.empty(max_frames + 1, dtype=torch.int64, device=self.device))
+                     for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream(device=self.device)
+        self.copied = [torch.cuda.Event(), torch.cuda.Event()]
+        self.free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.k = 0
+
+    def start(self, event: torch.cuda.Event):
+        self.copy_stream.wait_event(event)
+
+    def run(self, h_idx: torch.Tensor, h_off: torch.Tensor, fn):
+        i = self.k % 2
+        self.k += 1
+        d_idx, d_off = self.bufs[i]
+        if h_idx.numel() > d_idx.numel() or h_off.numel() > d_off.numel():
+            raise ValueError("step larger than the buffers")
+        cur = torch.cuda.current_stream(self.device)
+        self.copy_stream.wait_event(self.free[i])
+        with torch.cuda.stream(self.copy_stream):
+            di = d_idx[:h_idx.numel()]
+            do = d_off[:h_off.numel()]
+            di.copy_(h_idx, non_blocking=True)
+            do.copy_(h_off, non_blocking=True)
+            self.copied[i].record(self.copy_stream)
+        cur.wait_event(self.copied[i])
+        out = fn(di, do)
+        self.free[i].record(cur)
+        return out
