@@ -333,7 +333,7 @@ typedef struct eer4d_tuning {
   float   ms[3];
 } eer4d_tuning;
 /* Times the candidate shapes on the caller's data and keeps the fastest in the
- * plan: scatter (every tile size that fits shared memory x 1..3 CTAs/SM) over
+ * plan: scatter (16..128 frames per tile x 1..3 CTAs/SM) over
  * the whole CSR (d_idx, d_off for all scan_ny*scan_nx frames), the fused scan
  * DFT (1..4 CTAs/SM; plans without it keep 0) and the trotter kernel with the
  * aberrations d_aberr (double[5]) (1..3 CTAs/SM).  d_work, d_G and d_scratch
@@ -367,6 +367,12 @@ int eer4d_get_tuning(const eer4d_plan* plan, eer4d_tuning* h_tuning);
  * cudaEvent_t owned by the caller (NULL entries are skipped); passing NULL
  * arrays clears the hook. */
 int eer4d_set_stage_events(eer4d_plan* plan, void* const* ev_start, void* const* ev_stop);
+/* Failure-path self test: runs the bounded device wait of the fused scan DFT
+ * (the wait for a producer that has not arrived) on a counter that nothing
+ * increments.  After its limit (1 s) the wait gives up, sets
+ * EER4D_ST_TIMEOUT in d_status and the kernel returns; the context stays
+ * usable.  d_scratch: 8 bytes of device memory.  Enqueues one small kernel. */
+int eer4d_selftest_wait(void* d_scratch, uint32_t* d_status, void* stream);
 /* Number of kernels the library has launched in this process. */
 uint64_t eer4d_launch_count(void);
 

@@ -30,7 +30,7 @@ EXPORTS = [
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
     "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
     "virtual_detectors", "ssb_g_slices", "dpc_iterative", "eer4d_autotune", "eer4d_set_tuning",
-    "eer4d_get_tuning",
+    "eer4d_get_tuning", "eer4d_selftest_wait",
 ]
 MAX_SLICES = 64
 MAX_RINGS = 64
@@ -126,6 +126,7 @@ def load(path: str | None = None):
         "dpc_iterative": (I32, [P, P, D, D, D, I32, I32, P, S, P, P]),
         "eer4d_autotune": (I32, [P, P, U64, P, P, P, P, P, P, P, C.POINTER(Tuning)]),
         "eer4d_set_tuning": (I32, [P, C.POINTER(Tuning)]),
+        "eer4d_selftest_wait": (I32, [P, P, P]),
         "eer4d_get_tuning": (I32, [P, C.POINTER(Tuning)]),
         "ssb_g_slices": (I32, [P, P, C.POINTER(C.c_int32), I32, P, P]),
         "virtual_detectors": (I32, [P, P, U64, P, U64, C.POINTER(D), I32, P, D, D, P, P, P, P]),
@@ -374,3 +375,10 @@ def eer4d_get_tuning(plan: Plan) -> dict:
     t = Tuning()
     _check(load().eer4d_get_tuning(plan.handle, C.byref(t)), "eer4d_get_tuning")
     return t.as_dict()
+
+
+def eer4d_selftest_wait(scratch, status):
+    """Runs the library's bounded device wait against a counter that nothing
+    increments (see the header): status then holds EER4D_ST_TIMEOUT."""
+    _check(load().eer4d_selftest_wait(_ptr(scratch, "scratch"), _ptr(status, "status"), _stream()),
+           "eer4d_selftest_wait")

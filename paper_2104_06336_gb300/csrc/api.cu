@@ -120,7 +120,9 @@ void stage_end(const eer4d_plan* p, int stage, cudaStream_t s) {
   if (p && p->ev_stop[stage]) cudaEventRecord(p->ev_stop[stage], s);
 }
 cudaError_t ensure_smem(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the opt-in covers dynamic + static shared memory above 48 KB, so it is set
+  // for every sizeable dynamic request (static arrays of up to 16 KB beside it)
+  if (bytes <= 32 * 1024) return cudaSuccess;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> done;  // (kernel, device) -> bytes set
   std::lock_guard<std::mutex> lk(mu);
@@ -586,12 +588,10 @@ int eer4d_autotune(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
   const eer4d_tuning keep = p->tune;
   eer4d_tuning best = keep;
   int rc = EER4D_OK;
-  // scatter: tile sizes that fit shared memory x 1..3 resident CTAs per SM
+  // scatter: frames per tile 16..128 (pixels chunked to fit) x 1..3 CTAs per SM
   {
     float tbest = -1.f;
     for (int tf = 16; tf <= 128; tf *= 2) {
-      const size_t tile = (size_t)p->P_pad * (tf / 2 + 1) * 4;
-      if (tile > 160 * 1024) continue;
       for (int cps = 1; cps <= 3; ++cps) {
         p->tune = best;
         p->tune.scatter_tf = tf;
@@ -657,6 +657,12 @@ int eer4d_autotune(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
   if (rc == EER4D_OK) rc = cuda_fail(cudaStreamSynchronize(s));
   if (h_out) *h_out = p->tune;
   return rc;
+}
+
+int eer4d_selftest_wait(void* d_scratch, uint32_t* d_status, void* stream) {
+  if (!d_scratch || !d_status) return EER4D_EINVAL;
+  return cuda_fail(launch_wait_selftest(static_cast<unsigned*>(d_scratch), d_status,
+                                        (cudaStream_t)stream));
 }
 
 int ssb_trotter_counts(const eer4d_plan* p, const double* d_aberr, int32_t* d_count,

@@ -166,6 +166,7 @@ cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, 
 size_t work_counts_bytes(const eer4d_plan* p);
 size_t work_bytes(const eer4d_plan* p);
 bool dft2_fused_ok(const eer4d_plan* p);
+cudaError_t launch_wait_selftest(unsigned* ctl, uint32_t* st, cudaStream_t s);
 size_t dft2_ring_bytes(const eer4d_plan* p);
 size_t dft2_ctl_bytes(const eer4d_plan* p);
 cudaError_t launch_dft2_fused(const eer4d_plan* p, const __half* counts, float2* ring, float2* G,

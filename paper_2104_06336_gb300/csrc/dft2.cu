@@ -226,7 +226,21 @@ cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, fl
   return cudaGetLastError();
 }
 
+// The wait above on a counter that nothing increments: it must give up after
+// its time limit and report EER4D_ST_TIMEOUT (tests of the failure path).
+__global__ void k_wait_selftest(unsigned* ctl, uint32_t* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) wait_count(ctl, 1u, ctl + 1, st);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned* ctl, uint32_t* st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  k_wait_selftest<<<1, 32, 0, s>>>(ctl, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 bool dft2_fused_ok(const eer4d_plan* p) {
   const int N = (int)p->g.scan_nx;

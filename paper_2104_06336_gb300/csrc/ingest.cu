@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     uint64_t first, uint64_t nfr, uint32_t W, uint32_t H, DivMod dw,
     const int16_t* __restrict__ lutp, const int16_t* __restrict__ lutx,
     const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int ph, int P_pad,
-    int TF, uint64_t ntiles, int tab_smem, uint64_t NR, __half* counts, uint32_t* st) {
+    int TF, int PC, int NCH, uint64_t ntiles, int tab_smem, uint64_t NR, __half* counts,
+    uint32_t* st) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_lo[128];  // event range of each tile frame
   __shared__ uint32_t s_n[128];
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
   const uint32_t WH = W * H;
   const int TW = TF / 2;
   const int TP = TW + 1;
-  uint32_t* tile = smem;  // [P_pad][TP]
-  int16_t* tx = reinterpret_cast<int16_t*>(smem + (size_t)P_pad * TP);  // [W], [H], [ph*pw]
+  uint32_t* tile = smem;  // [PC][TP]: the pixels [p0, p0 + PC) of the tile
+  int16_t* tx = reinterpret_cast<int16_t*>(smem + (size_t)PC * TP);  // [W], [H], [ph*pw]
   int16_t* ty = tx + W;
   int16_t* t2 = ty + H;
   if (tab_smem) {
@@ -237,15 +238,21 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
   const int QW = TW / 2;  // 8-byte groups per pixel row (a power of two)
   const int qs = __ffs(QW) - 1;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t tf0 = T0 + t * TF;  // global frame of tile column 0
+    // tile t: frames of frame tile t / NCH, pixels of chunk t % NCH (the
+    // chunks of one frame tile are neighbours in t, so its events are read
+    // from L2 after the first chunk)
+    const uint64_t ft = t / NCH;
+    const int p0 = (int)(t - ft * NCH) * PC;
+    const int pc = P_pad - p0 < PC ? P_pad - p0 : PC;
+    const uint64_t tf0 = T0 + ft * TF;  // global frame of tile column 0
     // frames j of the tile inside the chunk: [j0, j1)
     const int j0 = tf0 < first ? (int)(first - tf0) : 0;
     const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
     __syncthreads();  // the previous tile is written out
     if (threadIdx.x == 0) s_maxev = 0;
     {
-      uint4* t4 = reinterpret_cast<uint4*>(tile);  // P_pad * TP is a multiple of 4 (P_pad % 16 == 0)
-      const int n4 = P_pad * TP / 4;
+      uint4* t4 = reinterpret_cast<uint4*>(tile);  // PC * TP is a multiple of 4 (PC % 16 == 0)
+      const int n4 = PC * TP / 4;
       for (int i = threadIdx.x; i < n4; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
@@ -292,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
             if (kk >= n4[f]) continue;
             const uint32_t e = v[2 * f + h];
             if (e >= WH) { ++drop; continue; }
-            const int pp = pixel(e);
-            if (pp >= 0) atomicAdd(col + pp * TP, inc);
+            const int pp = pixel(e) - p0;
+            if ((unsigned)pp < (unsigned)pc) atomicAdd(col + pp * TP, inc);
           }
         }
       }
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     // with every count below 1024, OR-ing 0x6400 (fp16 1024.0) into a 16-bit
     // count n gives the fp16 of 1024 + n exactly; subtracting 1024 gives n
     const __half2 k1024 = __floats2half2_rn(1024.f, 1024.f);
-    for (int i = threadIdx.x; i < P_pad * QW; i += blockDim.x) {
+    for (int i = threadIdx.x; i < pc * QW; i += blockDim.x) {
       const int p = i >> qs, w = i & (QW - 1);
       const uint32_t w0 = tile[p * TP + 2 * w], w1 = tile[p * TP + 2 * w + 1];
       __half2 h01, h23;
@@ -319,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
         h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
         h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
       }
-      __half* dst = counts + (size_t)p * NR + tf0 + 4 * w;
+      __half* dst = counts + (size_t)(p0 + p) * NR + tf0 + 4 * w;
       if (full) {
         uint2 pk;
         pk.x = *reinterpret_cast<const uint32_t*>(&h01);
@@ -352,10 +359,20 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
 #define EER4D_SCATTER_TILE_KB 40
 #endif
 constexpr size_t kScatterTabBytes = 64 * 1024;  // largest binning tables kept in shared memory
+
+// Frames per scatter tile: 32 (64-byte count rows) unless tuned; the pixels
+// are split into chunks whose padded tile PC x (TF/2 + 1) words fits the tile
+// budget (a crop larger than the budget is counted chunk by chunk, each chunk
+// re-reading the tile's events, from L2).
 int scatter_tf(int P_pad) {
-  int tf = 128;
-  while (tf > 4 && (size_t)P_pad * (tf / 2 + 1) * 4 > EER4D_SCATTER_TILE_KB * 1024) tf >>= 1;
-  return tf;
+  (void)P_pad;
+  return 32;
+}
+
+int scatter_pc(int P_pad, int TF) {
+  int pc = (int)((size_t)EER4D_SCATTER_TILE_KB * 1024 / ((size_t)(TF / 2 + 1) * 4)) / 16 * 16;
+  if (pc < 16) pc = 16;
+  return pc < P_pad ? pc : P_pad;
 }
 
 cudaError_t launch_validate(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
@@ -405,8 +422,10 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
                            uint32_t* st, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int TF = scatter_tf_for(p);
+  const int PC = scatter_pc(p->P_pad, TF);
+  const int NCH = (p->P_pad + PC - 1) / PC;
   const uint32_t W = p->g.det_w, H = p->g.det_h;
-  const size_t tile = (size_t)p->P_pad * (TF / 2 + 1) * 4;
+  const size_t tile = (size_t)PC * (TF / 2 + 1) * 4;
   const size_t tabs = ((size_t)W + H + (size_t)p->g.pw * p->g.ph) * 2;
   // binning tables in shared memory when they fit beside the tile (a raw-pixel
   // table in global memory otherwise, or the three global tables without it)
@@ -415,7 +434,7 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   cudaError_t e = ensure_smem((const void*)k_scatter, sm);
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;
-  const uint64_t tiles = (first + n - T0 + TF - 1) / TF;
+  const uint64_t tiles = (first + n - T0 + TF - 1) / TF * NCH;
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -428,7 +447,8 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   stage_begin(p, EER4D_STAGE_SCATTER, s);
   k_scatter<<<(unsigned)grid, kThreads, sm, s>>>(
       idx, n_idx, off, first, n, W, H, p->dw, p->d_lutp, p->d_lutx, p->d_luty, p->d_lut2,
-      (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, tiles, tab_smem, (uint64_t)p->cstride, counts, st);
+      (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, PC, NCH, tiles, tab_smem, (uint64_t)p->cstride,
+      counts, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_SCATTER, s);
   return cudaGetLastError();

@@ -289,6 +289,26 @@ def test_pixel_overflow_flagged():
     assert int(rec.status[0].item()) & P._lib.ST_OVERFLOW
 
 
+def test_bounded_wait_gives_up_and_reports(c1):
+    """Failure detection without a GPU fault: the fused DFT's device wait on a
+    producer that never arrives gives up after its limit (about 1 s), sets
+    EER4D_ST_TIMEOUT and returns; the context stays usable."""
+    import time
+    import paper_2104_06336_gb300 as P
+    scr = torch.zeros(2, dtype=torch.int32, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.time()
+    P.eer4d_selftest_wait(scr, st)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    assert P.status_code(st) == P._lib.EER4D_ETIMEOUT
+    assert 0.5 < dt < 30.0, dt
+    ph, var = c1.rec.reconstruct(torch.zeros(5, dtype=torch.float64))
+    torch.cuda.synchronize()
+    assert c1.rec.check() == 0 and torch.isfinite(ph).all()
+
+
 def test_out_of_order_chunks_rejected(c1):
     import paper_2104_06336_gb300 as P
     with pytest.raises(P.Eer4dError) as e:
@@ -457,6 +477,37 @@ def test_virtual_detectors_bit_exact(which, request):
         ref = orc.virtual_detector_counts(c.idx_np, c.off_np, W, H, radii, cx, cy)
         np.testing.assert_array_equal(got, ref)
     assert c.rec.check() == 0
+
+
+# ------------------------------------------- large crop, chunked scatter ----
+def test_large_crop_counts_and_phase():
+    """The 576x576 detector binned 6x cropped to the disk of radius 48 binned
+    pixels (7209 kept pixels, the residency variant of the full workload) on
+    a 48x48 scan: the scatter counts pixel chunk by chunk; counts bit-exact,
+    G to 2e-6 of max|G| and the SSB phase to 1e-5 relative L2."""
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(5, scan_ny=48, scan_nx=48)
+    geom = dict(synth.geometry(w), crop_px=48.0)
+    d = synth.generate(w, "cuda")
+    rec = P.Reconstructor(geom)
+    rec.load(d.idx, d.off)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    Pn, P_pad = rec.info["P"], rec.info["P_pad"]
+    assert Pn == 7209
+    idx, off = d.numpy()
+    ref = orc.densify(idx, off, geom)
+    counts = rec.counts.reshape(P_pad, -1)[:Pn].float().cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(counts, ref)
+    G = orc.g_function(ref, geom)
+    Gh = rec.G_complex().cpu().numpy()  # [nkx][P_pad][Ny]
+    nkx = w.scan_nx // 2 + 1
+    got = np.transpose(Gh[:, :Pn, :], (1, 2, 0))
+    assert np.abs(got - G[:, :, :nkx]).max() <= 2e-6 * np.abs(G).max()
+    ab = (40.0, 5.0, -5.0, 0.0, 0.0)
+    ph, _ = rec.reconstruct(torch.tensor(ab, dtype=torch.float64))
+    phi, _ = orc.ssb_phase(G, geom, ab, "none")
+    assert rel_l2(ph[0].cpu().numpy(), phi) <= 1e-5
 
 
 # ------------------------------------------- run-length-encoded ingest -----
