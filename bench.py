@@ -54,6 +54,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(ms: float, units_per_rank: int, world: int, device=None):
+    """Whole-job throughput of replicas: every rank processes units_per_rank
+    units; the job takes as long as its slowest rank (max over ranks of the
+    per-step time, an all-reduce when world > 1).  Returns (units/s, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return world * units_per_rank / (t_max * 1e-3), t_max
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -282,11 +295,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     ms = t_start.elapsed_time(t_stop) / args.steps
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = world * C / (ms * 1e-3)
+    value, ms = job_throughput(ms, C, world, device=dev)
     # a stage whose events were not recorded inside the timed region did not run
     ran = [t_start.elapsed_time(ev[0][i][0]) >= 0.0 for i in range(nst)]
     stage_ms = {n: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
@@ -397,13 +406,11 @@ def run_ours(args, rank, world, local_rank):
             pipe.run(h_idx, h_off, body)
         b.record()
         torch.cuda.synchronize()
-        e_ms = torch.tensor([a.elapsed_time(b) / args.steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
-        out["e2e"] = {"value": world * C / (float(e_ms.item()) * 1e-3), "unit": UNIT,
+        e_val, e_max = job_throughput(a.elapsed_time(b) / args.steps, C, world, device=dev)
+        out["e2e"] = {"value": e_val, "unit": UNIT,
                       "h2d_bytes_per_step": h_idx.numel() * 4 + h_off.numel() * 8,
                       "d2h_bytes_per_step": h_phase.numel() * 4 + 8,
-                      "ms_per_step": float(e_ms.item()),
+                      "ms_per_step": e_max,
                       "overlap": "upload of step k+1 on a copy stream during step k (StreamedSteps)"}
         assert torch.isfinite(h_phase).all()
 
