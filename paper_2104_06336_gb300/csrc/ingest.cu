@@ -97,8 +97,10 @@ __global__ void __launch_bounds__(kThreads) k_validate(const uint32_t* __restric
 // every fetched sector is used); no shared staging and no block barrier
 // before the sums.  Thread 0 computes the centre meanwhile.
 constexpr int kComThreads = 256;
+// frames of at most this many events sum x and y in 32 bits (x, y < 32768)
+constexpr uint64_t kComFast = 131071;
 
-__global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict__ idx, uint64_t n_idx,
+__global__ void __launch_bounds__(kComThreads, 8) k_com(const uint32_t* __restrict__ idx, uint64_t n_idx,
                                                      const uint64_t* __restrict__ off, uint32_t F,
                                                      uint32_t WH, DivMod dw,
                                                      const long long* __restrict__ totals,
@@ -135,7 +137,16 @@ __global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict_
       px += x; py += y; ++pn;
     };
     uint64_t i = lo;
-    if ((reinterpret_cast<uintptr_t>(idx) & 15) == 0) {
+    if (hi - lo > kComFast) {
+      // a frame too long for 32-bit sums (never at detector doses): 64-bit
+      for (; i < hi; ++i) {
+        const uint32_t v = __ldg(idx + i);
+        if (v >= WH) { ++drop; continue; }
+        uint32_t y, x;
+        dw.divmod(v, y, x);
+        sx += x; sy += y; ++sn;
+      }
+    } else if ((reinterpret_cast<uintptr_t>(idx) & 15) == 0) {
       for (; i < hi && (i & 3); ++i) one(__ldg(idx + i));
       for (; i + 16 <= hi; i += 16) {
         const uint4* q = reinterpret_cast<const uint4*>(idx + i);
@@ -151,7 +162,7 @@ __global__ void __launch_bounds__(kComThreads) k_com(const uint32_t* __restrict_
       }
     }
     for (; i < hi; ++i) one(__ldg(idx + i));
-    sx = px; sy = py; sn = pn;
+    sx += px; sy += py; sn += pn;
   }
   __syncthreads();  // the centre
   if (f < F) {
