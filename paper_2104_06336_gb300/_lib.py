@@ -149,6 +149,21 @@ def _ptr(t: torch.Tensor | None, name: str):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(t, nbytes: int, name: str, dtype=None):
+    """Host-side size (and dtype) check of a device buffer before its pointer
+    goes to the library, which cannot see buffer sizes."""
+    if t is None:
+        return
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{name} holds {have} bytes, needs {nbytes}")
+
+
+_U32 = (torch.int32, getattr(torch, "uint32", torch.int32))
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -180,6 +195,9 @@ class Plan:
         info = Info()
         _check(lib.eer4d_plan_info(h, C.byref(info)), "eer4d_plan_info")
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
+        self.F = int(geom["scan_ny"]) * int(geom["scan_nx"])
+        self.WH = int(geom["det_w"]) * int(geom["det_h"])
+        self.G_bytes = 8 * self.info["nkx"] * self.info["P_pad"] * int(geom["scan_ny"])
 
     @property
     def handle(self):
@@ -205,6 +223,11 @@ class Plan:
 
 # ---- entry points, same names as the C ABI ---------------------------------
 def eer_load_csr(plan: Plan, idx, off, pacbed=None, totals=None, status=None):
+    _need(idx, 0, "idx", _U32)
+    _need(off, 16, "off", torch.int64)
+    _need(pacbed, 8 * plan.WH, "pacbed", torch.int64)
+    _need(totals, 24, "totals", torch.int64)
+    _need(status, 16, "status")
     _check(load().eer_load_csr(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
                                off.numel() - 1, _ptr(pacbed, "pacbed"), _ptr(totals, "totals"),
                                _ptr(status, "status"), _stream()), "eer_load_csr")
@@ -212,6 +235,19 @@ def eer_load_csr(plan: Plan, idx, off, pacbed=None, totals=None, status=None):
 
 def com_dpc(plan: Plan, idx, off, sums, com, phase=None, totals=None, cx=0.0, cy=0.0, lam1=0.0,
             lam2=0.0, scratch=None, status=None):
+    F = plan.F
+    if off.numel() != F + 1:
+        raise ValueError("com_dpc takes the whole scan: off must have scan_ny*scan_nx + 1 entries")
+    _need(idx, 0, "idx", _U32)
+    _need(sums, 24 * F, "sums", torch.int64)
+    _need(com, 8 * F, "com", torch.float32)
+    _need(phase, 4 * F, "phase", torch.float32)
+    _need(totals, 24, "totals", torch.int64)
+    if phase is not None:
+        if scratch is None:
+            raise ValueError("com_dpc needs scratch (8 bytes per frame) for the phase")
+        _need(scratch, 8 * F, "scratch")
+    _need(status, 16, "status")
     _check(load().com_dpc(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
                           _ptr(sums, "sums"), _ptr(com, "com"), _ptr(phase, "phase"),
                           _ptr(totals, "totals"), float(cx), float(cy), float(lam1), float(lam2),
@@ -219,6 +255,11 @@ def com_dpc(plan: Plan, idx, off, sums, com, phase=None, totals=None, cx=0.0, cy
 
 
 def ssb_accumulate(plan: Plan, idx, off, first_frame: int, counts, G, is_last: bool, status=None):
+    _need(idx, 0, "idx", _U32)
+    _need(off, 8, "off", torch.int64)
+    _need(counts, plan.workspace_bytes(1)[0], "counts (workspace)")
+    _need(G, plan.G_bytes, "G")
+    _need(status, 16, "status")
     _check(load().ssb_accumulate(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
                                  int(first_frame), off.numel() - 1, _ptr(counts, "counts"),
                                  _ptr(G, "G"), int(bool(is_last)), _ptr(status, "status"),
@@ -227,18 +268,39 @@ def ssb_accumulate(plan: Plan, idx, off, first_frame: int, counts, G, is_last: b
 
 def ssb_reconstruct(plan: Plan, G, aberr, scratch, phase=None, var=None, status=None):
     n = aberr.numel() // 5
+    if n < 1 or aberr.numel() != 5 * n:
+        raise ValueError("aberr holds [n][5] float64 values")
+    _need(aberr, 40 * n, "aberr", torch.float64)
+    _need(G, plan.G_bytes, "G")
+    _need(scratch, plan.workspace_bytes(n)[2], "scratch")
+    _need(phase, 4 * n * plan.F, "phase", torch.float32)
+    _need(var, 8 * n, "var", torch.float64)
+    _need(status, 16, "status")
     _check(load().ssb_reconstruct(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"), n,
                                   _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
                                   _ptr(status, "status"), _stream()), "ssb_reconstruct")
 
 
 def ssb_grad(plan: Plan, G, aberr, grad_phase, grad, scratch, status=None):
+    _need(G, plan.G_bytes, "G")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(grad_phase, 4 * plan.F, "grad_phase", torch.float32)
+    _need(grad, 40, "grad", torch.float64)
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
+    _need(status, 16, "status")
     _check(load().ssb_grad(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
                            _ptr(grad_phase, "grad_phase"), _ptr(grad, "grad"),
                            _ptr(scratch, "scratch"), _ptr(status, "status"), _stream()), "ssb_grad")
 
 
 def ssb_variance_grad(plan: Plan, G, aberr, scratch, var, grad, phase=None, status=None):
+    _need(G, plan.G_bytes, "G")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
+    _need(var, 8, "var", torch.float64)
+    _need(grad, 40, "grad", torch.float64)
+    _need(phase, 4 * plan.F, "phase", torch.float32)
+    _need(status, 16, "status")
     _check(load().ssb_variance_grad(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
                                     _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
                                     _ptr(grad, "grad"), _ptr(status, "status"), _stream()),
@@ -246,11 +308,22 @@ def ssb_variance_grad(plan: Plan, G, aberr, scratch, var, grad, phase=None, stat
 
 
 def ssb_trotter_counts(plan: Plan, aberr, count, scratch):
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(count, 4 * plan.F, "count", torch.int32)
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
     _check(load().ssb_trotter_counts(plan.handle, _ptr(aberr, "aberr"), _ptr(count, "count"),
                                      _ptr(scratch, "scratch"), _stream()), "ssb_trotter_counts")
 
 
 def ssb_refocus_step(plan: Plan, G, aberr, step, scratch, var, grad, phase=None, status=None):
+    _need(G, plan.G_bytes, "G")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(step, 40, "step", torch.float64)
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
+    _need(var, 8, "var", torch.float64)
+    _need(grad, 40, "grad", torch.float64)
+    _need(phase, 4 * plan.F, "phase", torch.float32)
+    _need(status, 16, "status")
     _check(load().ssb_refocus_step(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"), _ptr(step, "step"),
                                    _ptr(scratch, "scratch"), _ptr(phase, "phase"), _ptr(var, "var"),
                                    _ptr(grad, "grad"), _ptr(status, "status"), _stream()),
@@ -275,6 +348,11 @@ def eer4d_launch_count() -> int:
 def ssb_reconstruct_static(plan: Plan, G, aberr, phase=None, var=None, status=None):
     """One-candidate ssb_reconstruct whose working memory is the library's
     static device array (no scratch argument, no allocation)."""
+    _need(G, plan.G_bytes, "G")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(phase, 4 * plan.F, "phase", torch.float32)
+    _need(var, 8, "var", torch.float64)
+    _need(status, 16, "status")
     _check(load().ssb_reconstruct_static(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
                                          _ptr(phase, "phase"), _ptr(var, "var"),
                                          _ptr(status, "status"), _stream()), "ssb_reconstruct_static")
@@ -299,6 +377,15 @@ def ssb_reconstruct_batched(plans, Gs, aberr, scratch, phases=None, var=None, st
     n = len(plans)
     if len(Gs) != n or aberr.numel() != 5 * n:
         raise ValueError("one G and one aberration row per plan")
+    _need(aberr, 40 * n, "aberr", torch.float64)
+    for pl, g in zip(plans, Gs):
+        _need(g, pl.G_bytes, "G")
+    _need(scratch, batched_scratch_bytes(plans), "scratch")
+    _need(var, 8 * n, "var", torch.float64)
+    _need(status, 16, "status")
+    if phases is not None:
+        for pl, ph in zip(plans, phases):
+            _need(ph, 4 * pl.F, "phase", torch.float32)
     g_arr = (C.c_void_p * n)(*[_ptr(g, "G").value for g in Gs])
     ph_arr = None
     if phases is not None:
@@ -318,6 +405,10 @@ def eer_decode_rle(runs, off, idx=None, status=None):
     ``idx=runs`` decodes in place)."""
     if idx is None:
         idx = torch.empty_like(runs)
+    _need(runs, 0, "runs", _U32)
+    _need(idx, 4 * runs.numel(), "idx", _U32)
+    _need(off, 8, "off", torch.int64)
+    _need(status, 16, "status")
     _check(load().eer_decode_rle(_ptr(runs, "runs"), runs.numel(), _ptr(off, "off"),
                                  off.numel() - 1, _ptr(idx, "idx"), _ptr(status, "status"),
                                  _stream()), "eer_decode_rle")
@@ -330,6 +421,9 @@ def virtual_detectors(plan: Plan, idx, off, radii, out, scratch, totals=None, cx
     about the PACBED centre (totals) or (cx, cy); out int32 [n_rings][F]."""
     r = [float(x) for x in radii]
     arr = (C.c_double * len(r))(*r)
+    _need(out, 4 * (len(r) - 1) * plan.F, "out", torch.int32)
+    _need(scratch, plan.WH, "scratch")
+    _need(status, 16, "status")
     _check(load().virtual_detectors(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
                                     off.numel() - 1, arr, len(r) - 1, _ptr(totals, "totals"),
                                     float(cx), float(cy), _ptr(scratch, "scratch"),
@@ -342,6 +436,8 @@ def ssb_g_slices(plan: Plan, G, bins, out):
     out complex64 [n][ph][pw] (as a float32 [n][ph][pw][2] or complex tensor)."""
     flat = [int(v) for b in bins for v in b]
     arr = (C.c_int32 * len(flat))(*flat)
+    _need(G, plan.G_bytes, "G")
+    _need(out, 8 * len(bins) * int(plan.geom["ph"]) * int(plan.geom["pw"]), "out")
     _check(load().ssb_g_slices(plan.handle, _ptr(G, "G"), arr, len(bins), _ptr(out, "out"),
                                _stream()), "ssb_g_slices")
 
@@ -349,6 +445,8 @@ def ssb_g_slices(plan: Plan, G, bins, out):
 def dpc_iterative(plan: Plan, com, phase, scratch, n_iter: int, mu: float = 0.5, lam1: float = 0.0,
                   lam2: float = 0.0, pad: int = 2):
     """Iterative regularised DPC from COM maps (float32 [2][F], raw px)."""
+    _need(com, 8 * plan.F, "com", torch.float32)
+    _need(phase, 4 * plan.F, "phase", torch.float32)
     _check(load().dpc_iterative(plan.handle, _ptr(com, "com"), float(lam1), float(lam2), float(mu),
                                 int(n_iter), int(pad), _ptr(scratch, "scratch"),
                                 scratch.numel() * scratch.element_size(), _ptr(phase, "phase"),
@@ -359,6 +457,11 @@ def eer4d_autotune(plan: Plan, idx, off, work, G, scratch, aberr, status=None) -
     """Times the launch-shape candidates on this data and keeps the fastest in
     the plan (synchronises the current stream).  Returns the choice."""
     t = Tuning()
+    _need(work, plan.workspace_bytes(1)[0], "work")
+    _need(G, plan.G_bytes, "G")
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(status, 16, "status")
     _check(load().eer4d_autotune(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
                                  _ptr(work, "work"), _ptr(G, "G"), _ptr(scratch, "scratch"),
                                  _ptr(aberr, "aberr"), _ptr(status, "status"), _stream(),
@@ -380,5 +483,7 @@ def eer4d_get_tuning(plan: Plan) -> dict:
 def eer4d_selftest_wait(scratch, status):
     """Runs the library's bounded device wait against a counter that nothing
     increments (see the header): status then holds EER4D_ST_TIMEOUT."""
+    _need(scratch, 8, "scratch")
+    _need(status, 16, "status")
     _check(load().eer4d_selftest_wait(_ptr(scratch, "scratch"), _ptr(status, "status"), _stream()),
            "eer4d_selftest_wait")
