@@ -309,6 +309,27 @@ def test_bounded_wait_gives_up_and_reports(c1):
     assert c1.rec.check() == 0 and torch.isfinite(ph).all()
 
 
+def test_binding_rejects_short_or_mistyped_buffers(c1):
+    """The library cannot see buffer sizes; the binding refuses a buffer that
+    is too short or of the wrong type before any launch."""
+    import paper_2104_06336_gb300 as P
+    rec = c1.rec
+    ab = torch.zeros(5, dtype=torch.float64, device="cuda")
+    short = torch.empty(rec.F - 1, dtype=torch.float32, device="cuda")
+    var = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        P.ssb_reconstruct(rec.plan, rec.G, ab, rec.scratch, short, var, status=rec.status)
+    with pytest.raises(TypeError):
+        P.ssb_reconstruct(rec.plan, rec.G, ab.float(), rec.scratch, None, var, status=rec.status)
+    with pytest.raises(ValueError):
+        P.ssb_reconstruct(rec.plan, rec.G[:10], ab, rec.scratch, None, var, status=rec.status)
+    with pytest.raises(ValueError):
+        P.com_dpc(rec.plan, c1.idx, c1.off[:-1], torch.empty(3, rec.F, dtype=torch.int64, device="cuda"),
+                  torch.empty(2, rec.F, device="cuda"))
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+
+
 def test_out_of_order_chunks_rejected(c1):
     import paper_2104_06336_gb300 as P
     with pytest.raises(P.Eer4dError) as e:
