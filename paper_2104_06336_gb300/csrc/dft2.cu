@@ -164,6 +164,22 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     }
     __syncthreads();
     if (!s_ok) break;
+    {
+      // the next task is known: if it is a DFT along x, pull its counts rows
+      // (gp rows of 2N bytes) from DRAM into L2 now, so its loads hit L2
+      const long long tn = s_t[(it + 1) % 3];
+      if (tn < q.total) {
+        const Task kn = decode(tn, q);
+        if (kn.type == 0) {
+          const int lines = q.N / 64;  // 128-byte lines per row
+          for (int i = threadIdx.x; i < q.gp * lines; i += NT) {
+            const int row = i / lines, line = i - row * lines;
+            const __half* a = counts + (size_t)(kn.g * q.gp + row) * q.F + (size_t)kn.r * q.N + line * 64;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+          }
+        }
+      }
+    }
     float2* slot = ring + (long long)(k.g % kRing) * q.slot;
     const int p0 = k.g * q.gp;
     if (k.type == 0) {
