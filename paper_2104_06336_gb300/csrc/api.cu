@@ -46,15 +46,19 @@ cudaError_t make_fft(int N, FftDesc& d, float2** dev) {
   d.N = N;
   d.nst = factorize(N, d.radix);
   if (d.nst < 0) return cudaErrorInvalidValue;
-  std::vector<float2> tw(N);
+  const int r1 = reg_r1(N), r2 = r1 ? N / r1 : 0;
+  std::vector<float2> tw(r1 ? 2 * N : N);
   const double tp = 6.283185307179586476925286766559;
   for (int j = 0; j < N; ++j) {
     tw[j] = make_float2((float)cos(tp * j / N), (float)-sin(tp * j / N));
   }
-  cudaError_t e = cudaMalloc(dev, sizeof(float2) * N);
+  for (int k1 = 0; k1 < r1; ++k1)
+    for (int j2 = 0; j2 < r2; ++j2) tw[N + k1 * r2 + j2] = tw[j2 * k1];  // j2 k1 < N
+  cudaError_t e = cudaMalloc(dev, sizeof(float2) * tw.size());
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(*dev, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(*dev, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
   d.tw = *dev;
+  d.tw4 = r1 ? *dev + N : nullptr;
   return e;
 }
 

@@ -40,13 +40,24 @@ struct DivMod {
 };
 
 // ---------------------------------------------------------------- FFT plan ---
+// First factor R1 of the register four-step split N = R1 * R2 (R1 >= R2) for
+// power-of-two N in [16, 1024], 0 for other lengths.
+__host__ __device__ constexpr int reg_r1(int N) {
+  return N == 1024 || N == 512 ? 32 : N == 256 || N == 128 ? 16 : N == 64 || N == 32 ? 8 : N == 16 ? 4 : 0;
+}
+
 // Stockham radix-decomposition of one transform length; twiddles tw[j] =
 // exp(-2 pi i j / N) made on the host in double from the exact integer j.
+// For the register four-step lengths, tw4[k1 * R2 + j2] = tw[j2 k1]
+// (R1 = reg_r1(N) rows of R2): a thread of the first pass (fixed j2) reads
+// its twiddles at constant offsets, and the lanes of a warp (consecutive j2)
+// read consecutive entries.
 struct FftDesc {
   int N;
   int nst;
   int radix[EER4D_MAX_STAGES];
   const float2* tw;
+  const float2* tw4;  // NULL unless reg_r1(N) > 0
 };
 
 // ------------------------------------------------------------- plan state ---
@@ -72,10 +83,10 @@ struct eer4d_plan {
   uint16_t* d_tl_q;
   int* d_tl_n;
   int tl_cap;
-  float2* d_tw_y;            // [scan_ny]
-  float2* d_tw_x;            // [scan_nx]
-  float2* d_tw_y2;           // [2 scan_ny] (zero-padded DPC grid)
-  float2* d_tw_x2;           // [2 scan_nx]
+  float2* d_tw_y;            // [scan_ny] (+ [scan_ny] four-step layout, FftDesc)
+  float2* d_tw_x;            // [scan_nx] (+ [scan_nx])
+  float2* d_tw_y2;           // [2 scan_ny] (+ [2 scan_ny]; zero-padded DPC grid)
+  float2* d_tw_x2;           // [2 scan_nx] (+ [2 scan_nx])
   FftDesc fy, fx, fy2, fx2;
   // streaming state of ssb_accumulate (host)
   uint64_t next_frame;

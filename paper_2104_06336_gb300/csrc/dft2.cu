@@ -36,7 +36,7 @@ constexpr unsigned kWaitIters = 1u << 24;
 struct Dft2Params {
   int N, nkx, P_pad, gp, n_groups, n1, n2;
   long long slot;   // float2 per ring slot
-  long long total;  // tasks
+  unsigned total;   // tasks (< 2^31)
   long long F;      // row stride of the counts (frames, padded)
 };
 
@@ -70,20 +70,23 @@ __device__ bool wait_count(const unsigned* cnt, unsigned target, unsigned* abort
 }
 
 struct Task {
-  int type;  // 0 = S1 (DFT along x of one scan row), 1 = S2 (DFT along y)
+  int type;  // 0 = S1 (DFT along x of one scan row), 1 = S2 (DFT along y), -1 = queue empty
   int g;     // pixel group
   int r;     // index within the group's tasks of that type
 };
 
-__device__ __forceinline__ Task decode(long long t, const Dft2Params& q) {
-  if (t < q.n1) return Task{0, 0, (int)t};
-  const long long u = t - q.n1;
-  const long long pair = (long long)q.n1 + q.n2;
-  const long long full = (long long)(q.n_groups - 1) * pair;
+// Queue index -> task (thread 0 only; 32-bit: the host keeps total < 2^31).
+__device__ __forceinline__ Task decode(unsigned t, const Dft2Params& q) {
+  if (t >= q.total) return Task{-1, 0, 0};
+  const unsigned n1 = q.n1;
+  if (t < n1) return Task{0, 0, (int)t};
+  const unsigned u = t - n1;
+  const unsigned pair = n1 + (unsigned)q.n2;
+  const unsigned full = (unsigned)(q.n_groups - 1) * pair;
   if (u < full) {
-    const int g = (int)(u / pair);
-    const int r = (int)(u - (long long)g * pair);
-    return r < q.n1 ? Task{0, g + 1, r} : Task{1, g, r - q.n1};
+    const unsigned g = u / pair;
+    const unsigned r = u - g * pair;
+    return r < n1 ? Task{0, (int)g + 1, (int)r} : Task{1, (int)g, (int)(r - n1)};
   }
   return Task{1, q.n_groups - 1, (int)(u - full)};
 }
@@ -117,11 +120,13 @@ __device__ __forceinline__ void publish(Pending& pd, unsigned* done1, unsigned* 
 template <int R1, int R2, int CP>
 __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     k_dft2_fused(const __half* __restrict__ counts, float2* ring, float2* G,
-                 const float2* __restrict__ twx, const float2* __restrict__ twy, Dft2Params q,
+                 const float2* __restrict__ twx4, const float2* __restrict__ twy4, Dft2Params q,
                  unsigned* ctl, uint32_t* st) {
   constexpr int NT = R1 * CP;
+  constexpr int N = R1 * R2;  // = q.N
+  constexpr int GP = 2 * CP;  // pixels per group, = q.gp
   extern __shared__ float2 sm[];
-  __shared__ long long s_t[3];
+  __shared__ Task s_k[3];
   __shared__ int s_ok;
   unsigned* next = ctl;
   unsigned* abort_flag = ctl + 1;
@@ -131,23 +136,22 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
   __shared__ Pending pd;
   __shared__ int known1, known2;  // groups seen complete (S1, S2)
   // The queue is read two tasks ahead: the index taken in iteration i is kept
-  // in a register and stored for iteration i + 2 only in iteration i + 1, so
-  // thread 0 never waits for the atomic's reply.
+  // in a register and decoded into s_k for iteration i + 2 only in iteration
+  // i + 1, so thread 0 never waits for the atomic's reply.
   unsigned inflight = 0;
   if (threadIdx.x == 0) {
     pd.type = pd.g = -1;
     pd.n = 0;
     known1 = known2 = -1;
-    s_t[0] = atomicAdd(next, 1u);
-    s_t[1] = atomicAdd(next, 1u);
+    s_k[0] = decode(atomicAdd(next, 1u), q);
+    s_k[1] = decode(atomicAdd(next, 1u), q);
   }
   for (int it = 0;; ++it) {
     __syncthreads();  // the previous task is finished by every thread
-    const long long t = s_t[it % 3];
-    if (t >= q.total) break;
-    const Task k = decode(t, q);
+    const Task k = s_k[it % 3];
+    if (k.type < 0) break;
     if (threadIdx.x == 0) {
-      if (it > 0) s_t[(it + 1) % 3] = inflight;
+      if (it > 0) s_k[(it + 1) % 3] = decode(inflight, q);
       inflight = atomicAdd(next, 1u);
       if (pd.n && (pd.type != k.type || pd.g != k.g)) publish(pd, done1, done2);
       bool ok = true;
@@ -166,36 +170,34 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     if (!s_ok) break;
     {
       // the next task is known: if it is a DFT along x, pull its counts rows
-      // (gp rows of 2N bytes) from DRAM into L2 now, so its loads hit L2
-      const long long tn = s_t[(it + 1) % 3];
-      if (tn < q.total) {
-        const Task kn = decode(tn, q);
-        if (kn.type == 0) {
-          const int lines = q.N / 64;  // 128-byte lines per row
-          for (int i = threadIdx.x; i < q.gp * lines; i += NT) {
-            const int row = i / lines, line = i - row * lines;
-            const __half* a = counts + (size_t)(kn.g * q.gp + row) * q.F + (size_t)kn.r * q.N + line * 64;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-          }
+      // (GP rows of 2N bytes) from DRAM into L2 now, so its loads hit L2
+      const Task kn = s_k[(it + 1) % 3];
+      if (kn.type == 0) {
+        constexpr int lines = N / 64;  // 128-byte lines per row
+        for (int i = threadIdx.x; i < GP * lines; i += NT) {
+          const int row = i / lines, line = i - row * lines;
+          const __half* a = counts + (size_t)(kn.g * GP + row) * q.F + (size_t)kn.r * N + line * 64;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
         }
       }
     }
     float2* slot = ring + (long long)(k.g % kRing) * q.slot;
-    const int p0 = k.g * q.gp;
+    const int p0 = k.g * GP;
     if (k.type == 0) {
-      // S1: the gp pixel rows of scan row r, DFT along x into the slot
-      rowfft_r2c_tile<R1, R2, CP, true>(counts, slot, twx, q.P_pad, p0, p0, k.r, q.F, q.N,
-                                        (long long)q.N * q.gp, 1, q.gp, sm);
+      // S1: the GP pixel rows of scan row r, DFT along x into the slot
+      rowfft_r2c_tile<R1, R2, CP, true, true>(counts, slot, twx4, q.P_pad, p0, p0, k.r, q.F, N,
+                                              (long long)N * GP, 1, GP, sm);
     } else {
-      // S2: all gp pixel columns of K_x = r, DFT along y into G, CP at a time
-      const float2* blk = slot + (long long)k.r * q.N * q.gp;
-      float2* gout = G + ((long long)k.r * q.P_pad + p0) * q.N;
-      for (int c0 = 0; c0 < q.gp; c0 += CP) {
+      // S2: all GP pixel columns of K_x = r, DFT along y into G, CP at a time
+      const float2* blk = slot + (long long)k.r * N * GP;
+      float2* gout = G + ((long long)k.r * q.P_pad + p0) * N;
+#pragma unroll
+      for (int c0 = 0; c0 < GP; c0 += CP) {
         if (c0) __syncthreads();
-        colfft_tile<R1, R2, CP, 1, true, true>(blk, gout, twy, c0, q.gp, q.gp, q.N, 1.f, sm);
+        colfft_tile<R1, R2, CP, 1, true, true>(blk, gout, twy4, c0, GP, GP, N, 1.f, sm);
       }
       __syncthreads();
-      l2_discard(blk, sizeof(float2) * (size_t)q.N * q.gp, threadIdx.x, NT);
+      l2_discard(blk, sizeof(float2) * (size_t)N * GP, threadIdx.x, NT);
     }
     if (threadIdx.x == 0) {
       pd.type = k.type;
@@ -229,14 +231,17 @@ cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, fl
   q.n1 = N;
   q.n2 = p->nkx;
   q.slot = (long long)p->nkx * N * q.gp;
-  q.total = (long long)q.n_groups * (q.n1 + q.n2);
+  const long long total = (long long)q.n_groups * (q.n1 + q.n2);
+  if (total >= (1ll << 31)) return cudaErrorInvalidValue;
+  q.total = (unsigned)total;
   q.F = p->cstride;
   if ((e = cudaMemsetAsync(ctl, 0, ctl_bytes, s)) != cudaSuccess) return e;
   int cps = per_sm > 0 ? per_sm : 1;
   if (p->tune.dft_ctas_per_sm > 0 && p->tune.dft_ctas_per_sm < cps) cps = p->tune.dft_ctas_per_sm;
   long long grid = (long long)cps * nsm;
-  if (grid > q.total) grid = q.total;
-  k_dft2_fused<R1, R2, CP><<<(unsigned)grid, NT, sm, s>>>(counts, ring, G, p->fx.tw, p->fy.tw, q,
+  if (grid > (long long)q.total) grid = q.total;
+  if (!p->fx.tw4 || !p->fy.tw4) return cudaErrorInvalidValue;
+  k_dft2_fused<R1, R2, CP><<<(unsigned)grid, NT, sm, s>>>(counts, ring, G, p->fx.tw4, p->fy.tw4, q,
                                                           ctl, st);
   count_launches(1);
   return cudaGetLastError();

@@ -243,7 +243,8 @@ cudaError_t cols_reg_t(const FftDesc& d, const float2* in, float2* out, int ncol
   cudaError_t e = set_smem(kern, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((ncols + CB - 1) / CB, nbatch);
-  kern<<<grid, NT, sm, s>>>(in, out, d.tw, ncols, ld_in, ld_out, bs_in, bs_out, scale);
+  if (!d.tw4 || reg_r1(d.N) != R1) return cudaErrorInvalidValue;
+  kern<<<grid, NT, sm, s>>>(in, out, d.tw4, ncols, ld_in, ld_out, bs_in, bs_out, scale);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -277,7 +278,8 @@ cudaError_t r2c_reg_t(const FftDesc& d, const __half* in, float2* out, int nA, i
   cudaError_t e = set_smem(kern, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((nA + 2 * CP - 1) / (2 * CP), nc);
-  kern<<<grid, R1 * CP, sm, s>>>(in, out, d.tw, nA, c0, in_sa, in_sc, out_skx, out_sa, out_sc);
+  if (!d.tw4 || reg_r1(d.N) != R1) return cudaErrorInvalidValue;
+  kern<<<grid, R1 * CP, sm, s>>>(in, out, d.tw4, nA, c0, in_sa, in_sc, out_skx, out_sa, out_sc);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -44,6 +44,14 @@ __host__ __device__ constexpr int bitrev_c(int i, int bits) {
 }
 __host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c(n / 2); }
 
+// Complex sum and difference as packed two-lane fp32 operations (one
+// instruction each); a - b is formed as fma(b, -1, a), which rounds once,
+// exactly like the scalar subtraction.
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 // In-register R-point DFT (R a power of two <= 32), natural order in and out:
 // radix-2 decimation in frequency, then the bit-reversal permutation (free
 // register renaming once unrolled).  DIR = +1 forward, -1 inverse (unscaled).
@@ -56,8 +64,8 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
       for (int j = 0; j < span; ++j) {
         const float2 a = v[blk + j], b = v[blk + j + span];
-        v[blk + j] = make_float2(a.x + b.x, a.y + b.y);
-        const float2 d = make_float2(a.x - b.x, a.y - b.y);
+        v[blk + j] = cadd2(a, b);
+        const float2 d = csub2(a, b);
         const int m = j * (32 / (2 * span));  // twiddle exp(-+2 pi i m / 32)
         if (j == 0) {
           v[blk + j + span] = d;
@@ -125,8 +133,9 @@ __device__ __forceinline__ int colfft_yidx(int k1, int col, int j2) {
 template <int R1, int R2, int CB, int DIR, bool TOUT, bool STREAM,
           int NTH = (R1 > R2 ? R1 : R2) * CB>
 __device__ __forceinline__ void colfft_tile(const float2* in, float2* out,
-                                            const float2* __restrict__ tw, int c0, int ncols,
+                                            const float2* __restrict__ tw4, int c0, int ncols,
                                             int ld_in, int ld_out, float scale, float2* sm) {
+  static_assert(R1 == reg_r1(R1 * R2), "twiddle layout of FftDesc::tw4");
   for (int g = threadIdx.x; g < R2 * CB; g += NTH) {
     const int col = g % CB, j2 = g / CB, c = c0 + col;
     float2 v[R1];
@@ -137,7 +146,7 @@ __device__ __forceinline__ void colfft_tile(const float2* in, float2* out,
     dft_reg<R1, DIR>(v);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const float2 t = (k1 == 0) ? v[k1] : cmul(v[k1], twid_dir(tw, j2 * k1, DIR));
+      const float2 t = (k1 == 0) ? v[k1] : cmul(v[k1], twid_dir(tw4, k1 * R2 + j2, DIR));
       sm[colfft_yidx<R1, R2, CB, DIR, TOUT>(k1, col, j2)] = t;
     }
   }
@@ -168,10 +177,10 @@ __device__ __forceinline__ void colfft_tile(const float2* in, float2* out,
 // CTA x covers columns [x*CB, x*CB + CB), batch = blockIdx.y.
 template <int R1, int R2, int CB, int DIR, bool TOUT>
 __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB, 768 / ((R1 > R2 ? R1 : R2) * CB))
-    k_colfft_reg(const float2* in, float2* out, const float2* __restrict__ tw, int ncols, int ld_in,
+    k_colfft_reg(const float2* in, float2* out, const float2* __restrict__ tw4, int ncols, int ld_in,
                  int ld_out, long long bs_in, long long bs_out, float scale) {
   extern __shared__ float2 sm[];
-  colfft_tile<R1, R2, CB, DIR, TOUT, false>(in + blockIdx.y * bs_in, out + blockIdx.y * bs_out, tw,
+  colfft_tile<R1, R2, CB, DIR, TOUT, false>(in + blockIdx.y * bs_in, out + blockIdx.y * bs_out, tw4,
                                            blockIdx.x * CB, ncols, ld_in, ld_out, scale, sm);
 }
 
@@ -182,17 +191,19 @@ __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB, 768 / ((R1 > R2 ? R1
 // rows z = row_2b + i row_2b+1; A(k) = (Z(k) + conj Z(-k))/2,
 // B(k) = -i (Z(k) - conj Z(-k))/2.  Requires R1 >= R2 so pass 2 has exactly
 // one (k1, b) group per thread.  `sm` holds max(R1*CP*(R2+1), N*CP) float2.
-template <int R1, int R2, int CP, bool STREAM>
+// FULL: the caller guarantees a0 + 2*CP <= nA (no bounds tests).
+template <int R1, int R2, int CP, bool STREAM, bool FULL = false>
 __device__ __forceinline__ void rowfft_r2c_tile(const __half* __restrict__ in, float2* out,
-                                                const float2* __restrict__ tw, int nA, int a0,
+                                                const float2* __restrict__ tw4, int nA, int a0,
                                                 int a_out0, int c, long long in_sa,
                                                 long long in_sc, long long out_skx,
                                                 long long out_sa, long long out_sc, float2* sm) {
   static_assert(R1 >= R2, "R1 >= R2");
+  static_assert(R1 == reg_r1(R1 * R2), "twiddle layout of FftDesc::tw4");
   constexpr int N = R1 * R2;
   constexpr int NT = R1 * CP;
   constexpr int PITCH = R2 + 1;
-  const bool full = a0 + 2 * CP <= nA;  // every pixel row of the tile exists
+  const bool full = FULL || a0 + 2 * CP <= nA;  // every pixel row of the tile exists
   for (int g = threadIdx.x; g < R2 * CP; g += NT) {
     const int j2 = g % R2, b = g / R2;
     const int ra = a0 + 2 * b, rb = ra + 1;
@@ -214,7 +225,7 @@ __device__ __forceinline__ void rowfft_r2c_tile(const __half* __restrict__ in, f
     dft_reg<R1, 1>(v);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const float2 t = (k1 == 0) ? v[k1] : cmul(v[k1], __ldg(tw + j2 * k1));
+      const float2 t = (k1 == 0) ? v[k1] : cmul(v[k1], __ldg(tw4 + k1 * R2 + j2));
       sm[(k1 * CP + b) * PITCH + j2] = t;
     }
   }
@@ -237,17 +248,17 @@ __device__ __forceinline__ void rowfft_r2c_tile(const __half* __restrict__ in, f
   for (int w = threadIdx.x; w < NK * CP; w += NT) {
     const int b = w % CP, k = w / CP;
     const int a = a0 + 2 * b;
-    if (a >= nA) continue;
+    if (!FULL && a >= nA) continue;
     const float2 z = sm[k * CP + b];
     const float2 zm = sm[((N - k) & (N - 1)) * CP + b];
     const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
     const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
     float2* o = out + k * out_skx + (a - a_out0) * out_sa + c * out_sc;
-    if (out_sa == 1 && a + 1 < nA) {
+    if (out_sa == 1 && (FULL || a + 1 < nA)) {
       *reinterpret_cast<float4*>(o) = make_float4(A.x, A.y, B.x, B.y);
     } else {
       o[0] = A;
-      if (a + 1 < nA) o[out_sa] = B;
+      if (FULL || a + 1 < nA) o[out_sa] = B;
     }
   }
 }
@@ -255,10 +266,10 @@ __device__ __forceinline__ void rowfft_r2c_tile(const __half* __restrict__ in, f
 // CTA (x, y) takes pixels [2*CP*x, 2*CP*x + 2*CP) at scan row c0 + y.
 template <int R1, int R2, int CP>
 __global__ void __launch_bounds__(R1 * CP, 768 / (R1 * CP))
-    k_rowfft_r2c_reg(const __half* __restrict__ in, float2* out, const float2* __restrict__ tw,
+    k_rowfft_r2c_reg(const __half* __restrict__ in, float2* out, const float2* __restrict__ tw4,
                      int nA, int c0, long long in_sa, long long in_sc, long long out_skx,
                      long long out_sa, long long out_sc) {
   extern __shared__ float2 sm[];
-  rowfft_r2c_tile<R1, R2, CP, false>(in, out, tw, nA, blockIdx.x * 2 * CP, 0, c0 + blockIdx.y,
+  rowfft_r2c_tile<R1, R2, CP, false>(in, out, tw4, nA, blockIdx.x * 2 * CP, 0, c0 + blockIdx.y,
                                      in_sa, in_sc, out_skx, out_sa, out_sc, sm);
 }
