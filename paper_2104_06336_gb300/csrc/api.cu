@@ -96,6 +96,7 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_tl_mask);
   cudaFree(p->d_tl_q);
   cudaFree(p->d_tl_n);
+  cudaFree(p->d_tl_order);
   cudaFree(p->d_tw_y);
   cudaFree(p->d_tw_x);
   cudaFree(p->d_tw_y2);
@@ -268,9 +269,11 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
     cudaFree(p->d_tl_mask);
     cudaFree(p->d_tl_q);
     cudaFree(p->d_tl_n);
+    cudaFree(p->d_tl_order);
     p->d_tl_mask = nullptr;
     p->d_tl_q = nullptr;
     p->d_tl_n = nullptr;
+    p->d_tl_order = nullptr;
   }
   if (precision == EER4D_SPLIT_FP16 && (e = make_dftx_tc(p)) != cudaSuccess) {
     const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);

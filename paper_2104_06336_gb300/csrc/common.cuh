@@ -82,6 +82,7 @@ struct eer4d_plan {
   uint2* d_tl_mask;          // trotter membership lists at rotation 0 (NULL: none)
   uint16_t* d_tl_q;
   int* d_tl_n;
+  int* d_tl_order;           // warp tasks by decreasing list length (work-queue order)
   int tl_cap;
   float2* d_tw_y;            // [scan_ny] (+ [scan_ny] four-step layout, FftDesc)
   float2* d_tw_x;            // [scan_nx] (+ [scan_nx])

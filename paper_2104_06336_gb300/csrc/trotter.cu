@@ -23,6 +23,9 @@
 // the transform of the real image phi: phi = IFFT2(H) with H Hermitian, so
 // the inverse is a real (C2R) transform and V = sum_b |H(b)|^2 / N_R^2
 // (Parseval).  The aberration-weighted spectrum is never written to memory.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -58,9 +61,10 @@ __device__ __forceinline__ float chi_turns(const CandCoef& c, float qx, float qy
 // rotation in another row is flagged.
 __global__ void k_prep(const double* __restrict__ aberr, int n_cand, const short2* __restrict__ pix,
                        int P_pad, int P, double dalpha, double lambda, CandCoef* coef, float2* ek,
-                       uint32_t* st, int own_rot = 0) {
+                       uint32_t* st, int own_rot = 0, unsigned* qctr = nullptr) {
   __shared__ CandCoef sc;
   const int c = blockIdx.x;
+  if (qctr && c == 0 && threadIdx.x == 0) *qctr = 0u;  // the trotter's work queue
   if (threadIdx.x == 0) {
     const double* a = aberr + 5 * c;
     const double d2 = dalpha * dalpha;
@@ -172,7 +176,8 @@ __global__ void __launch_bounds__(kWarps * 32,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
               const float2* __restrict__ W, float2* H, double* partial, int32_t* count,
               const uint2* __restrict__ tl_mask, const uint16_t* __restrict__ tl_q,
-              const int* __restrict__ tl_n, int tl_cap) {
+              const int* __restrict__ tl_n, const int* __restrict__ tl_order, int tl_cap,
+              unsigned* qctr) {
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
   extern __shared__ unsigned char smem_raw[];
   float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
@@ -213,7 +218,18 @@ __global__ void __launch_bounds__(kWarps * 32,
 #pragma unroll
     for (int c = 0; c < NC; ++c) cf[c] = coef[cb + (c < ncp ? c : 0)];
 
-    for (int t = gw; t < ntask; t += nwarps) {
+    // Warp tasks come from a work queue (with the lists, longest first) when
+    // there is one pass and no gradient sums (whose order would then vary
+    // between runs); otherwise warp gw takes tasks gw, gw + nwarps, ...
+    const bool dyn = !GRAD && npass == 1 && qctr != nullptr;
+    auto take = [&]() -> int {
+      unsigned v = 0u;
+      if (lane == 0) v = atomicAdd(qctr, 1u);
+      return (int)__shfl_sync(0xffffffffu, v, 0);
+    };
+    const int* order = (dyn && lists) ? tl_order : nullptr;
+    for (int u = dyn ? take() : gw; u < ntask; u = dyn ? take() : u + nwarps) {
+      const int t = order ? __ldg(order + u) : u;
       const int mx = t / nyw;
       const int my = (t - mx * nyw) * 32 + lane;
       const bool active = my < P.Ny;
@@ -661,7 +677,7 @@ int trot_blocks(const eer4d_plan* p, const void* kern, size_t smem) {
 }
 
 struct Layout {
-  size_t coef, ek, gscale, H, partial, vpart, total;
+  size_t coef, ek, gscale, H, partial, vpart, queue, total;
 };
 Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   Layout L;
@@ -673,6 +689,7 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   L.H = o; o = align256(o + sizeof(float2) * (size_t)nh * p->g.scan_ny * p->nkx);
   L.partial = o; o = align256(o + sizeof(double) * 5 * kMaxTrotBlocks);
   L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)nh);
+  L.queue = o; o = align256(o + sizeof(unsigned));
   L.total = o;
   return L;
 }
@@ -680,7 +697,8 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
 template <int MODE, int NC>
 cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
                      const CandCoef* coef, const float2* ek, const double* gsc, const float2* W,
-                     float2* H, double* partial, int32_t* count, int* nblk, cudaStream_t s) {
+                     float2* H, double* partial, int32_t* count, unsigned* qctr, int* nblk,
+                     cudaStream_t s) {
   const size_t sm = sizeof(float2) * p->P_bf + sizeof(int) * ((p->P_bf + 1) & ~1) +
                     sizeof(float2) * (size_t)NC * p->P_bf;
   const void* kern = (const void*)k_trotter<MODE, NC>;
@@ -689,7 +707,7 @@ cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
   *nblk = trot_blocks(p, kern, sm);
   k_trotter<MODE, NC><<<*nblk, kWarps * 32, sm, s>>>(tp, G, p->d_bfp, p->d_pix, coef, ek, gsc, W,
                                                      H, partial, count, p->d_tl_mask, p->d_tl_q,
-                                                     p->d_tl_n, p->tl_cap);
+                                                     p->d_tl_n, p->d_tl_order, p->tl_cap, qctr);
   return cudaGetLastError();
 }
 
@@ -717,10 +735,11 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   float2* H = reinterpret_cast<float2*>(sb + L.H);
   double* partial = reinterpret_cast<double*>(sb + L.partial);
   double* vpart = reinterpret_cast<double*>(sb + L.vpart);
+  unsigned* qctr = reinterpret_cast<unsigned*>(sb + L.queue);
   cudaError_t e;
   stage_begin(p, EER4D_STAGE_TROTTER, s);
   k_prep<<<n_cand, 256, 0, s>>>(aberr, n_cand, p->d_pix, p->P_pad, p->P, p->g.dalpha_rad,
-                                p->g.lambda_A, coef, ek, st);
+                                p->g.lambda_A, coef, ek, st, 0, qctr);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mode != TROT_COUNT) {
@@ -738,17 +757,17 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   switch (mode) {
     case TROT_FWD:
       e = n_cand == 1
-              ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s)
-              : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+              ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s)
+              : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
       break;
     case TROT_GRAD:
-      e = launch_k<TROT_GRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      e = launch_k<TROT_GRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
       break;
     case TROT_VARGRAD:
-      e = launch_k<TROT_VARGRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      e = launch_k<TROT_VARGRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
       break;
     default:
-      e = launch_k<TROT_COUNT, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, &nblk, s);
+      e = launch_k<TROT_COUNT, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
       break;
   }
   count_launches(1);
@@ -942,5 +961,15 @@ cudaError_t build_trotter_lists(eer4d_plan* p) {
       (float)(p->g.k0_px * p->g.k0_px), p->d_bfp, p->d_pix, p->d_tl_mask, p->d_tl_q, p->d_tl_n,
       cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return cudaStreamSynchronize(0);
+  if ((e = cudaStreamSynchronize(0)) != cudaSuccess) return e;
+  // work-queue order: longest lists first (a task's time grows with its list),
+  // so the last tasks handed out are short and the warps finish together
+  std::vector<int> n(tasks), order(tasks);
+  if ((e = cudaMemcpy(n.data(), p->d_tl_n, tasks * sizeof(int), cudaMemcpyDeviceToHost)) !=
+      cudaSuccess)
+    return e;
+  for (size_t i = 0; i < tasks; ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  if ((e = cudaMalloc(&p->d_tl_order, tasks * sizeof(int))) != cudaSuccess) return e;
+  return cudaMemcpy(p->d_tl_order, order.data(), tasks * sizeof(int), cudaMemcpyHostToDevice);
 }
