@@ -21,9 +21,15 @@
 // co-residency of CTAs.  Waits are bounded (1 s on %globaltimer and an
 // iteration cap); a wait that gives up sets EER4D_ST_TIMEOUT and an abort
 // flag that ends every CTA's loop.
+#include <algorithm>
+
 #include "fft_reg.cuh"
 
 namespace {
+
+#ifndef EER4D_DFT2_S1_WARP
+#define EER4D_DFT2_S1_WARP 1  // N = 1024: warp-private four-step passes of the S1 tile
+#endif
 
 #ifndef EER4D_DFT2_MINB
 #define EER4D_DFT2_MINB 4  // resident CTAs per SM the register budget is sized for
@@ -117,6 +123,54 @@ __device__ __forceinline__ void publish(Pending& pd, unsigned* done1, unsigned* 
   pd.type = pd.g = -1;
 }
 
+// S1 tile for N = 1024 (R1 = R2 = 32) with one warp per complex row pair:
+// warp w transforms z = row(p0 + 2w) + i row(p0 + 2w + 1) of scan row r.
+// Pass 1 (lane = j2) and pass 2 (lane = k1) exchange through the warp's own
+// region of shared memory, so they need only __syncwarp; one CTA barrier then
+// makes the CP spectra visible to the half-spectrum split, which writes the
+// slot [k][r][GP] with one 16-byte store per (k, pair).
+constexpr int kW32Pitch = 33;                 // pass-1 rows (k1) of 32 + 1 float2
+constexpr int kW32Region = 32 * kW32Pitch + 4;  // float2 per warp (+4: pairs in distinct banks)
+
+template <int CP>
+__device__ __forceinline__ void s1_tile_w32(const __half* __restrict__ counts, float2* slot,
+                                            const float2* __restrict__ tw4, int p0, int r,
+                                            long long F, float2* sm) {
+  constexpr int N = 1024, GP = 2 * CP, NT = 32 * CP;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* rg = sm + w * kW32Region;
+  float2 v[32];
+  {
+    const __half* pa = counts + (size_t)(p0 + 2 * w) * F + (size_t)r * N + lane;
+    const __half* pb = pa + F;
+#pragma unroll
+    for (int j1 = 0; j1 < 32; ++j1)
+      v[j1] = make_float2(ld_h<true>(pa + 32 * j1), ld_h<true>(pb + 32 * j1));
+  }
+  dft_reg<32, 1>(v);
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1)
+    rg[k1 * kW32Pitch + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], __ldg(tw4 + k1 * 32 + lane));
+  __syncwarp();
+#pragma unroll
+  for (int j2 = 0; j2 < 32; ++j2) v[j2] = rg[lane * kW32Pitch + j2];
+  dft_reg<32, 1>(v);
+  __syncwarp();  // every lane has read the region before it is overwritten
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) rg[lane + 32 * k2] = v[k2];  // Z(k1 + 32 k2)
+  __syncthreads();
+  constexpr int NK = N / 2 + 1;
+  for (int i = threadIdx.x; i < NK * CP; i += NT) {
+    const int b = i % CP, k = i / CP;
+    const float2 z = sm[b * kW32Region + k];
+    const float2 zm = sm[b * kW32Region + ((N - k) & (N - 1))];
+    const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+    *reinterpret_cast<float4*>(slot + (size_t)k * N * GP + (size_t)r * GP + 2 * b) =
+        make_float4(A.x, A.y, B.x, B.y);
+  }
+}
+
 template <int R1, int R2, int CP>
 __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     k_dft2_fused(const __half* __restrict__ counts, float2* ring, float2* G,
@@ -185,8 +239,11 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     const int p0 = k.g * GP;
     if (k.type == 0) {
       // S1: the GP pixel rows of scan row r, DFT along x into the slot
-      rowfft_r2c_tile<R1, R2, CP, true, true>(counts, slot, twx4, q.P_pad, p0, p0, k.r, q.F, N,
-                                              (long long)N * GP, 1, GP, sm);
+      if constexpr (R1 == 32 && R2 == 32 && EER4D_DFT2_S1_WARP)
+        s1_tile_w32<CP>(counts, slot, twx4, p0, k.r, q.F, sm);
+      else
+        rowfft_r2c_tile<R1, R2, CP, true, true>(counts, slot, twx4, q.P_pad, p0, p0, k.r, q.F, N,
+                                                (long long)N * GP, 1, GP, sm);
     } else {
       // S2: all GP pixel columns of K_x = r, DFT along y into G, CP at a time
       const float2* blk = slot + (long long)k.r * N * GP;
@@ -196,7 +253,8 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
         if (c0) __syncthreads();
         colfft_tile<R1, R2, CP, 1, true, true>(blk, gout, twy4, c0, GP, GP, N, 1.f, sm);
       }
-      __syncthreads();
+      // every load of the block happens in a first pass, before the tile's
+      // barrier, so every thread is past the block's last read here
       l2_discard(blk, sizeof(float2) * (size_t)N * GP, threadIdx.x, NT);
     }
     if (threadIdx.x == 0) {
@@ -213,7 +271,8 @@ cudaError_t launch_t(const eer4d_plan* p, const __half* counts, float2* ring, fl
                      unsigned* ctl, size_t ctl_bytes, uint32_t* st, cudaStream_t s) {
   constexpr int N = R1 * R2, NT = R1 * CP;
   const size_t a = (size_t)R1 * CP * (R2 + 1) + 2 * CP, b = (size_t)N * CP;
-  const size_t sm = sizeof(float2) * (a > b ? a : b);
+  const size_t c = (size_t)CP * kW32Region;
+  const size_t sm = sizeof(float2) * std::max(std::max(a, b), c);
   auto kern = k_dft2_fused<R1, R2, CP>;
   cudaError_t e = ensure_smem((const void*)kern, sm);
   if (e != cudaSuccess) return e;
