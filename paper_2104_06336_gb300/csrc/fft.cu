@@ -391,9 +391,48 @@ cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cud
   return cols(p->fy, W, W, 1, nkx, nkx, nkx, bs, bs, 1, 1.f, s);
 }
 
+template <int R1, int R2, int CB, int DIR, bool REAL_OUT>
+cudaError_t rows_reg_t(const FftDesc& d, float2* data, float* real_out, int rows, float scale,
+                       cudaStream_t s) {
+  constexpr int NT = (R1 > R2 ? R1 : R2) * CB;
+  const size_t sm = sizeof(float2) * (size_t)CB * R1 * (R2 + 1);
+  auto kern = k_rowfft_c2c_reg<R1, R2, CB, DIR, REAL_OUT>;
+  cudaError_t e = set_smem(kern, sm);
+  if (e != cudaSuccess) return e;
+  if (!d.tw4 || reg_r1(d.N) != R1) return cudaErrorInvalidValue;
+  kern<<<(rows + CB - 1) / CB, NT, sm, s>>>(data, real_out, d.tw4, rows, d.N, scale);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Register four-step transform of every row of [rows][d.N] in place (or its
+// real part times scale into real_out); d.N a register length (reg_size).
+template <int DIR, bool REAL_OUT = false>
+cudaError_t rows_reg(const FftDesc& d, float2* data, float* real_out, int rows, float scale,
+                     cudaStream_t s) {
+#define EER4D_ROWS(R1, R2, CB) return rows_reg_t<R1, R2, CB, DIR, REAL_OUT>(d, data, real_out, rows, scale, s)
+  switch (d.N) {
+    case 1024: EER4D_ROWS(32, 32, 4);
+    case 512: EER4D_ROWS(32, 16, 4);
+    case 256: EER4D_ROWS(16, 16, 8);
+    case 128: EER4D_ROWS(16, 8, 8);
+    case 64: EER4D_ROWS(8, 8, 16);
+    case 32: EER4D_ROWS(8, 4, 16);
+    default: EER4D_ROWS(4, 4, 32);
+  }
+#undef EER4D_ROWS
+}
+
 cudaError_t launch_fft2_c2c(const FftDesc& fy, const FftDesc& fx, float2* data, int dir,
                             float scale, cudaStream_t s) {
   const int My = fy.N, Mx = fx.N;
+  if (reg_size(Mx) && reg_size(My)) {
+    cudaError_t e = dir > 0 ? rows_reg<1>(fx, data, nullptr, My, 1.f, s)
+                            : rows_reg<-1>(fx, data, nullptr, My, 1.f, s);
+    if (e != cudaSuccess) return e;
+    return dir > 0 ? cols_reg<1>(fy, data, data, Mx, Mx, Mx, 0, 0, 1, scale, s)
+                   : cols_reg<-1>(fy, data, data, Mx, Mx, Mx, 0, 0, 1, scale, s);
+  }
   const int nb = rows_nb(Mx);
   const size_t sm = (size_t)2 * nb * Mx * sizeof(float2);
   cudaError_t e = set_smem(k_rows_c2c, sm);
@@ -413,12 +452,25 @@ cudaError_t launch_idpc(const eer4d_plan* p, float2* z, float* phase, double lam
   cudaError_t e = set_smem(k_rows_c2c, sm);
   if (e != cudaSuccess) return e;
   stage_begin(p, EER4D_STAGE_DPC, s);
+  const float inv_lx = (float)(1.0 / ((double)Nx * p->g.step_A));
+  const float inv_ly = (float)(1.0 / ((double)Ny * p->g.step_A));
+  if (reg_size(Nx) && reg_size(Ny)) {
+    // register four-step tiles: rows, columns (in place), filter, columns, rows
+    if ((e = rows_reg<1>(dx, z, nullptr, Ny, 1.f, s)) != cudaSuccess) return e;
+    if ((e = cols_reg<1>(p->fy, z, z, Nx, Nx, Nx, 0, 0, 1, 1.f, s)) != cudaSuccess) return e;
+    k_idpc_filter<<<(Ny * Nx + 255) / 256, 256, 0, s>>>(z, Ny, Nx, inv_lx, inv_ly, (float)lam1,
+                                                         (float)lam2);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cols_reg<-1>(p->fy, z, z, Nx, Nx, Nx, 0, 0, 1, 1.f, s)) != cudaSuccess) return e;
+    e = rows_reg<-1, true>(dx, z, phase, Ny, 1.f / ((float)Ny * (float)Nx), s);
+    stage_end(p, EER4D_STAGE_DPC, s);
+    return e;
+  }
   k_rows_c2c<<<(Ny + nb - 1) / nb, kThreads, sm, s>>>(z, nullptr, dx, Ny, nb, 1, 1.f);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cols(p->fy, z, z, 1, Nx, Nx, Nx, 0, 0, 1, 1.f, s)) != cudaSuccess) return e;
-  const float inv_lx = (float)(1.0 / ((double)Nx * p->g.step_A));
-  const float inv_ly = (float)(1.0 / ((double)Ny * p->g.step_A));
   k_idpc_filter<<<(Ny * Nx + 255) / 256, 256, 0, s>>>(z, Ny, Nx, inv_lx, inv_ly, (float)lam1,
                                                        (float)lam2);
   count_launches(1);

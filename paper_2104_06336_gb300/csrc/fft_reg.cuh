@@ -184,6 +184,49 @@ __global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB, 768 / ((R1 > R2 ? R1
                                            blockIdx.x * CB, ncols, ld_in, ld_out, scale, sm);
 }
 
+// Complex rows of a row-major array (element n of row r at r*ld + n), CB rows
+// per CTA from row blockIdx.x * CB, in place: every input of the CTA is read
+// in pass 1, before the barrier, and every output written in pass 2, after
+// it.  Pass 1 lanes run along j2 (unit stride), pass 2 lanes along k1.  With
+// REAL_OUT the real part times scale goes to real_out[r*ld + n] instead.
+template <int R1, int R2, int CB, int DIR, bool REAL_OUT>
+__global__ void __launch_bounds__((R1 > R2 ? R1 : R2) * CB, 768 / ((R1 > R2 ? R1 : R2) * CB))
+    k_rowfft_c2c_reg(float2* data, float* real_out, const float2* __restrict__ tw4, int rows,
+                     int ld, float scale) {
+  static_assert(R1 == reg_r1(R1 * R2), "twiddle layout of FftDesc::tw4");
+  constexpr int NTH = (R1 > R2 ? R1 : R2) * CB;
+  constexpr int PITCH = R2 + 1;
+  extern __shared__ float2 sm[];
+  const int r0 = blockIdx.x * CB;
+  for (int g = threadIdx.x; g < R2 * CB; g += NTH) {
+    const int b = g / R2, j2 = g % R2, r = r0 + b;
+    const float2* src = data + (size_t)r * ld + j2;
+    float2 v[R1];
+#pragma unroll
+    for (int j1 = 0; j1 < R1; ++j1) v[j1] = r < rows ? src[R2 * j1] : make_float2(0.f, 0.f);
+    dft_reg<R1, DIR>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      sm[(b * R1 + k1) * PITCH + j2] =
+          (k1 == 0) ? v[k1] : cmul(v[k1], twid_dir(tw4, k1 * R2 + j2, DIR));
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < R1 * CB; g += NTH) {
+    const int b = g / R1, k1 = g % R1, r = r0 + b;
+    float2 v[R2];
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) v[j2] = sm[(b * R1 + k1) * PITCH + j2];
+    dft_reg<R2, DIR>(v);
+    if (r >= rows) continue;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const size_t o = (size_t)r * ld + k1 + R1 * k2;
+      if (REAL_OUT) real_out[o] = v[k2].x * scale;
+      else data[o] = make_float2(v[k2].x * scale, v[k2].y * scale);
+    }
+  }
+}
+
 // Real rows (fp16 counts) -> half spectra, scan DFT along x of the G function.
 // Row (a, c) = (pixel, scan row y) starts at a*in_sa + c*in_sc; spectrum value
 // k goes to k*out_skx + (a - a_out0)*out_sa + c*out_sc.  The tile takes 2*CP
