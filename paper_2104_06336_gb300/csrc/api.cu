@@ -93,8 +93,8 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_pix);
   cudaFree(p->d_bfp);
   cudaFree(p->d_rows);
-  cudaFree(p->d_tl_mask);
-  cudaFree(p->d_tl_q);
+  cudaFree(p->d_tl_bits);
+  cudaFree(p->d_tl_qp);
   cudaFree(p->d_tl_n);
   cudaFree(p->d_tl_order);
   cudaFree(p->d_tw_y);
@@ -266,12 +266,12 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   // trotter membership lists at rotation 0 when they are small enough to keep
   if (trotter_lists_bytes(p) <= kTrotterListsMaxBytes && build_trotter_lists(p) != cudaSuccess) {
     cudaGetLastError();  // lists are optional: without them the kernel evaluates the masks
-    cudaFree(p->d_tl_mask);
-    cudaFree(p->d_tl_q);
+    cudaFree(p->d_tl_bits);
+    cudaFree(p->d_tl_qp);
     cudaFree(p->d_tl_n);
     cudaFree(p->d_tl_order);
-    p->d_tl_mask = nullptr;
-    p->d_tl_q = nullptr;
+    p->d_tl_bits = nullptr;
+    p->d_tl_qp = nullptr;
     p->d_tl_n = nullptr;
     p->d_tl_order = nullptr;
   }

@@ -79,8 +79,8 @@ struct eer4d_plan {
   __half* d_dft_hi;          // split-FP16 DFT matrix along x (tile-blocked), SPLIT_FP16 plans
   __half* d_dft_lo;
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
-  uint2* d_tl_mask;          // trotter membership lists at rotation 0 (NULL: none)
-  uint16_t* d_tl_q;
+  uint32_t* d_tl_bits;       // trotter membership lists at rotation 0 (NULL: none)
+  uint32_t* d_tl_qp;
   int* d_tl_n;
   int* d_tl_order;           // warp tasks by decreasing list length (work-queue order)
   int tl_cap;

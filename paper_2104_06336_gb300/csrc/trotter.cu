@@ -24,6 +24,7 @@
 // the inverse is a real (C2R) transform and V = sum_b |H(b)|^2 / N_R^2
 // (Parseval).  The aberration-weighted spectrum is never written to memory.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -170,12 +171,12 @@ __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, in
 // (|K(K)| per bin).
 template <int MODE, int NC>
 __global__ void __launch_bounds__(kWarps * 32,
-                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : (NC > 1 ? 3 : 4))
+                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 3)
     k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
               const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
               const float2* __restrict__ W, float2* H, double* partial, int32_t* count,
-              const uint2* __restrict__ tl_mask, const uint16_t* __restrict__ tl_q,
+              const uint32_t* __restrict__ tl_bits, const uint32_t* __restrict__ tl_qp,
               const int* __restrict__ tl_n, const int* __restrict__ tl_order, int tl_cap,
               unsigned* qctr) {
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
@@ -293,9 +294,12 @@ __global__ void __launch_bounds__(kWarps * 32,
         }
       };
 
-      // A batch of kBatch pixels q[i] with this lane's membership bits: every
-      // member's G load is issued before any is used (kBatch loads in flight).
-      auto batch = [&](unsigned mP, unsigned mM, const int (&qv)[kBatch]) {
+      // A batch of kBatch bright-field pixels with this lane's membership bits:
+      // every member's G load is issued before any is used (kBatch loads in
+      // flight).  Entry xv[i] is q << 16 | p (bright-field index, kept pixel)
+      // from the lists (PACKED), or the index q itself.
+      auto batch = [&](unsigned mP, unsigned mM, const uint32_t (&xv)[kBatch], auto packed) {
+        constexpr bool PACKED = decltype(packed)::value;
         nP += __popc(mP);
         nM += __popc(mM);
         if (MODE == TROT_COUNT) return;
@@ -304,12 +308,14 @@ __global__ void __launch_bounds__(kWarps * 32,
         float2 gb[kBatch];
 #pragma unroll
         for (int i = 0; i < kBatch; ++i)
-          gb[i] = ((mAny >> i) & 1u) ? Gl[(size_t)sp[qv[i]] * P.Ny] : make_float2(0.f, 0.f);
+          gb[i] = ((mAny >> i) & 1u)
+                      ? Gl[(size_t)(PACKED ? (int)(xv[i] & 0xffffu) : sp[xv[i]]) * P.Ny]
+                      : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
           if (!(memP || memM)) continue;
-          const int q = qv[i];
+          const int q = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
           const float2 kk = skk[q];
           const float2 g = gb[i];
           // Off Nyquist the two sets are disjoint, so one term per pixel: G into
@@ -326,40 +332,39 @@ __global__ void __launch_bounds__(kWarps * 32,
       };
       if (lists) {
         // only the pixels with a member among the warp's bins, in ascending
-        // q, with the 32 lanes' bits (the same sums in the same order)
+        // q (the same sums in the same order), 32 entries at a time: each
+        // lane reads its own two membership words (bit i = entry e0 + i) and
+        // one packed (q, p) entry, which the shuffles hand to every lane
         const int n = tl_n[t];
-        const uint2* mk = tl_mask + (size_t)t * tl_cap;
-        const uint16_t* qq = tl_q + (size_t)t * tl_cap;
-        for (int e0 = 0; e0 < n; e0 += kBatch) {
-          unsigned mP = 0u, mM = 0u;
-          int qv[kBatch];
+        const uint32_t* bits = tl_bits + (size_t)t * (tl_cap / 32) * 64;
+        const uint32_t* qps = tl_qp + (size_t)t * tl_cap;
+        for (int e0 = 0; e0 < n; e0 += 32) {
+          const uint32_t wP = __ldg(bits + 2 * e0 + lane);
+          const uint32_t wM = __ldg(bits + 2 * e0 + 32 + lane);
+          const uint32_t ql = __ldg(qps + e0 + lane);  // tl_cap is a multiple of 32
+          const int m = n - e0 < 32 ? n - e0 : 32;
+          for (int s0 = 0; s0 < m; s0 += kBatch) {
+            uint32_t xv[kBatch];
 #pragma unroll
-          for (int i = 0; i < kBatch; ++i) {
-            qv[i] = 0;
-            if (e0 + i < n) {
-              const uint2 m = __ldg(mk + e0 + i);
-              qv[i] = __ldg(qq + e0 + i);
-              mP |= ((m.x >> lane) & 1u) << i;
-              mM |= ((m.y >> lane) & 1u) << i;
-            }
+            for (int i = 0; i < kBatch; ++i) xv[i] = __shfl_sync(0xffffffffu, ql, s0 + i);
+            batch((wP >> s0) & 0xffu, (wM >> s0) & 0xffu, xv, std::true_type{});
           }
-          batch(mP, mM, qv);
         }
       } else {
         for (int q0 = 0; q0 < P.P_bf; q0 += kBatch) {
           unsigned mP = 0u, mM = 0u;
-          int qv[kBatch];
+          uint32_t xv[kBatch];
 #pragma unroll
           for (int i = 0; i < kBatch; ++i) {
             const int q = q0 + i;
-            qv[i] = q < P.P_bf ? q : 0;
+            xv[i] = q < P.P_bf ? q : 0;
             if (q >= P.P_bf) continue;
             bool memP, memM;
             member_bits(skk[q], Kpx, Kpy, Kmx, Kmy, nyq, active, P.k0sq, memP, memM);
             mP |= (unsigned)memP << i;
             mM |= (unsigned)memM << i;
           }
-          batch(mP, mM, qv);
+          batch(mP, mM, xv, std::false_type{});
         }
       }
 
@@ -706,7 +711,7 @@ cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
   if (e != cudaSuccess) return e;
   *nblk = trot_blocks(p, kern, sm);
   k_trotter<MODE, NC><<<*nblk, kWarps * 32, sm, s>>>(tp, G, p->d_bfp, p->d_pix, coef, ek, gsc, W,
-                                                     H, partial, count, p->d_tl_mask, p->d_tl_q,
+                                                     H, partial, count, p->d_tl_bits, p->d_tl_qp,
                                                      p->d_tl_n, p->d_tl_order, p->tl_cap, qctr);
   return cudaGetLastError();
 }
@@ -895,17 +900,21 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
 
 // ---- membership lists at scan rotation 0 (built once per plan) --------------
 // For every warp task (32 consecutive stored bins) the bright-field pixels with
-// a member among the task's bins, in ascending q, with two 32-bit masks (bit l
-// = bin my0 + l is a member of K(K'(b)) / K(K'(-b))), decided by the same
-// member_bits() the trotter kernel runs.  The trotter kernel then walks only
-// these pixels when the scan rotation is 0 (mask evaluation is about half of
-// its work).
+// a member among the task's bins, in ascending q, decided by the same
+// member_bits() the trotter kernel runs.  Entry e of task t is
+// qp[t][e] = q << 16 | p (bright-field index, kept pixel), and for each chunk
+// of 32 entries lane l of the task owns two words, bits[t][chunk][0][l] and
+// bits[t][chunk][1][l], whose bit i says whether bin my0 + l is a member of
+// K(K'(b)) / K(K'(-b)) through entry 32 chunk + i.  The trotter kernel then
+// walks only these pixels when the scan rotation is 0 (mask evaluation is
+// about half of its work).
 namespace {
 __global__ void __launch_bounds__(256) k_trot_lists(int Ny, int Nx, int nkx, int P_bf,
                                                     float kpm_x, float kpm_y, float k0sq,
                                                     const int32_t* __restrict__ bfp,
-                                                    const short2* __restrict__ pix, uint2* mask,
-                                                    uint16_t* qlist, int* nlist, int cap) {
+                                                    const short2* __restrict__ pix,
+                                                    uint32_t* bits, uint32_t* qp, int* nlist,
+                                                    int cap) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int nyw = (Ny + 31) >> 5;
@@ -923,43 +932,60 @@ __global__ void __launch_bounds__(256) k_trot_lists(int Ny, int Nx, int nkx, int
   kprime(c0, kpm_x, kpm_y, freq_index(mx, Nx), freq_index(mys, Ny), Kpx, Kpy);
   kprime(c0, kpm_x, kpm_y, freq_index(mmx, Nx), freq_index(mmy, Ny), Kmx, Kmy);
   const bool nyq = (2 * mx == Nx) || (2 * mys == Ny);
+  uint32_t* tb = bits + (size_t)t * (cap / 32) * 64;
+  uint32_t* tq = qp + (size_t)t * cap;
   int n = 0;
+  uint32_t wP = 0u, wM = 0u;
   for (int q = 0; q < P_bf; ++q) {  // same trip count on every lane
-    const short2 k = pix[bfp[q]];
+    const int p = bfp[q];
+    const short2 k = pix[p];
     bool memP, memM;
     member_bits(make_float2((float)k.x, (float)k.y), Kpx, Kpy, Kmx, Kmy, nyq, active, k0sq, memP,
                 memM);
     const unsigned bp = __ballot_sync(0xffffffffu, memP);
     const unsigned bm = __ballot_sync(0xffffffffu, memM);
-    if ((bp | bm) != 0u) {
-      if (lane == 0 && n < cap) {
-        mask[(size_t)t * cap + n] = make_uint2(bp, bm);
-        qlist[(size_t)t * cap + n] = (uint16_t)q;
+    if ((bp | bm) != 0u) {  // warp-uniform
+      wP |= (uint32_t)memP << (n & 31);
+      wM |= (uint32_t)memM << (n & 31);
+      if (lane == 0) tq[n] = (uint32_t)q << 16 | (uint32_t)p;
+      if ((n & 31) == 31) {
+        tb[2 * (n & ~31) + lane] = wP;
+        tb[2 * (n & ~31) + 32 + lane] = wM;
+        wP = wM = 0u;
       }
       ++n;
     }
   }
-  if (lane == 0) nlist[t] = n < cap ? n : cap;
+  if (n & 31) {
+    tb[2 * (n & ~31) + lane] = wP;
+    tb[2 * (n & ~31) + 32 + lane] = wM;
+  }
+  if (lane == 0) nlist[t] = n;
 }
 }  // namespace
 
+static size_t lists_cap(const eer4d_plan* p) { return ((size_t)p->P_bf + 31) / 32 * 32; }
+
 size_t trotter_lists_bytes(const eer4d_plan* p) {
   const size_t tasks = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
-  return tasks * (size_t)p->P_bf * (sizeof(uint2) + sizeof(uint16_t)) + tasks * sizeof(int);
+  return tasks * lists_cap(p) * (2 * sizeof(uint32_t) + sizeof(uint32_t)) + 2 * tasks * sizeof(int);
 }
 
 cudaError_t build_trotter_lists(eer4d_plan* p) {
   const size_t tasks = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
-  const int cap = p->P_bf;
+  const size_t cap = lists_cap(p);
+  if (p->P_pad > 65535) return cudaErrorInvalidValue;  // (q, p) packed in 16 bits each
   cudaError_t e;
-  if ((e = cudaMalloc(&p->d_tl_mask, tasks * cap * sizeof(uint2))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&p->d_tl_q, tasks * cap * sizeof(uint16_t))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p->d_tl_bits, tasks * cap * 2 * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p->d_tl_qp, tasks * cap * sizeof(uint32_t))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&p->d_tl_n, tasks * sizeof(int))) != cudaSuccess) return e;
-  p->tl_cap = cap;
+  // entries past a task's count are never used (their bits are 0); zero them anyway
+  if ((e = cudaMemset(p->d_tl_qp, 0, tasks * cap * sizeof(uint32_t))) != cudaSuccess) return e;
+  p->tl_cap = (int)cap;
   k_trot_lists<<<(unsigned)((tasks + 7) / 8), 256>>>(
       (int)p->g.scan_ny, (int)p->g.scan_nx, p->nkx, p->P_bf, (float)p->g.kpm_x, (float)p->g.kpm_y,
-      (float)(p->g.k0_px * p->g.k0_px), p->d_bfp, p->d_pix, p->d_tl_mask, p->d_tl_q, p->d_tl_n,
-      cap);
+      (float)(p->g.k0_px * p->g.k0_px), p->d_bfp, p->d_pix, p->d_tl_bits, p->d_tl_qp, p->d_tl_n,
+      (int)cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(0)) != cudaSuccess) return e;
   // work-queue order: longest lists first (a task's time grows with its list),
