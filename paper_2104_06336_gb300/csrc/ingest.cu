@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     uint64_t first, uint64_t nfr, uint32_t W, uint32_t H, DivMod dw,
     const int16_t* __restrict__ lutp, const int16_t* __restrict__ lutx,
     const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int ph, int P_pad,
-    int TF, int PC, int NCH, uint64_t ntiles, int tab_smem, uint64_t NR, __half* counts,
+    int TF, int PC, DivMod nch, uint32_t ntiles, int tab_smem, uint64_t NR, __half* counts,
     uint32_t* st) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_lo[128];  // event range of each tile frame
@@ -248,14 +248,15 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
   const uint64_t end = first + nfr;
   const int QW = TW / 2;  // 8-byte groups per pixel row (a power of two)
   const int qs = __ffs(QW) - 1;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // tile t: frames of frame tile t / NCH, pixels of chunk t % NCH (the
     // chunks of one frame tile are neighbours in t, so its events are read
     // from L2 after the first chunk)
-    const uint64_t ft = t / NCH;
-    const int p0 = (int)(t - ft * NCH) * PC;
+    uint32_t ft, ch;
+    nch.divmod(t, ft, ch);
+    const int p0 = (int)ch * PC;
     const int pc = P_pad - p0 < PC ? P_pad - p0 : PC;
-    const uint64_t tf0 = T0 + ft * TF;  // global frame of tile column 0
+    const uint64_t tf0 = T0 + (uint64_t)ft * TF;  // global frame of tile column 0
     // frames j of the tile inside the chunk: [j0, j1)
     const int j0 = tf0 < first ? (int)(first - tf0) : 0;
     const int j1 = tf0 + TF > end ? (int)(end - tf0) : TF;
@@ -446,6 +447,9 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;
   const uint64_t tiles = (first + n - T0 + TF - 1) / TF * NCH;
+  if (tiles >= (1ull << 31)) return cudaErrorInvalidValue;  // 32-bit tile indices in the kernel
+  DivMod nch;
+  nch.init((uint32_t)NCH);
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -458,7 +462,7 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   stage_begin(p, EER4D_STAGE_SCATTER, s);
   k_scatter<<<(unsigned)grid, kThreads, sm, s>>>(
       idx, n_idx, off, first, n, W, H, p->dw, p->d_lutp, p->d_lutx, p->d_luty, p->d_lut2,
-      (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, PC, NCH, tiles, tab_smem, (uint64_t)p->cstride,
+      (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, PC, nch, (uint32_t)tiles, tab_smem, (uint64_t)p->cstride,
       counts, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_SCATTER, s);
