@@ -4,9 +4,12 @@
 Workload: 1024x1024 scan, 576x576 detector binned 6x to 96x96 and cropped to
 the bright-field disk (553 pixels), 50 e-/frame (about 5.2e7 uint32 events,
 uint64 CSR offsets), seeded synthetic data.  One step = the whole hot path:
-eer_load_csr (validate + PACBED totals) -> com_dpc (COM sums + Fourier
-integrated DPC) -> ssb_accumulate (bin/crop/densify + scan DFT -> G) ->
-ssb_reconstruct (trotter + aberration phase + inverse transform + variance).
+ssb_accumulate_com (one pass over the events: offset and index checks,
+bin/crop/densify, per-frame COM sums and PACBED totals; then the scan DFT ->
+G) -> com_dpc_sums (COM maps + Fourier-integrated DPC) -> ssb_reconstruct
+(trotter + aberration phase + inverse transform + variance).
+``--separate-passes`` times the same outputs through eer_load_csr ->
+com_dpc -> ssb_accumulate (three passes over the events) instead.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -43,6 +46,8 @@ def parse():
     ap.add_argument("--refocus-steps", type=int, default=220)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--separate-passes", action="store_true",
+                    help="validate, COM and scatter as three passes over the events")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes instead of timing the candidates first")
     ap.add_argument("--no-forms", action="store_true",
@@ -212,13 +217,15 @@ STAGE_BYTES_DOC = {
 }
 
 
-def stage_bytes(C, F, P_pad, Ny, nkx, sigma_k):
+def stage_bytes(C, F, P_pad, Ny, nkx, sigma_k, single_pass=False):
     half = Ny * nkx
     return {
         "validate": 4 * C + 8 * (F + 1),
-        "com": 4 * C + 8 * (F + 1) + 40 * F,
+        # single pass: COM maps from the sums (24 B/frame in, 16 B/frame out)
+        "com": 40 * F if single_pass else 4 * C + 8 * (F + 1) + 40 * F,
         "dpc": 12 * F,
-        "scatter": 4 * C + 8 * (F + 1) + 2 * P_pad * F,
+        # single pass: the scatter also writes the sums (24 B/frame)
+        "scatter": 4 * C + 8 * (F + 1) + 2 * P_pad * F + (24 * F if single_pass else 0),
         "dft_x": 2 * P_pad * F + 8 * P_pad * half,
         "dft_y": 16 * P_pad * half,
         "trotter": 8 * sigma_k + 8 * half,
@@ -259,10 +266,16 @@ def run_ours(args, rank, world, local_rank):
 
     def step(ix, of):
         rec.totals.zero_()
-        P.eer_load_csr(rec.plan, ix, of, totals=rec.totals, status=rec.status)
-        P.com_dpc(rec.plan, ix, of, sums, com, dpc, totals=rec.totals, scratch=rec.scratch,
-                  status=rec.status)
-        P.ssb_accumulate(rec.plan, ix, of, 0, rec.work, rec.G, True, status=rec.status)
+        if args.separate_passes:
+            P.eer_load_csr(rec.plan, ix, of, totals=rec.totals, status=rec.status)
+            P.com_dpc(rec.plan, ix, of, sums, com, dpc, totals=rec.totals, scratch=rec.scratch,
+                      status=rec.status)
+            P.ssb_accumulate(rec.plan, ix, of, 0, rec.work, rec.G, True, status=rec.status)
+        else:
+            P.ssb_accumulate_com(rec.plan, ix, of, 0, rec.work, rec.G, True, sums, rec.totals,
+                                 status=rec.status)
+            P.com_dpc_sums(rec.plan, sums, com, dpc, totals=rec.totals, scratch=rec.scratch,
+                           status=rec.status)
         P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, phase, var, status=rec.status)
 
     nst = len(P._lib.STAGES)
@@ -303,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
     # algorithmic bytes of each stage; sigma_k = sum over bins of |K(K)|
     cnt = rec.trotter_counts(0.0)
     sigma_k = int(cnt.sum().item())
-    sb = stage_bytes(C, F, P_pad, Ny, nkx, sigma_k)
+    sb = stage_bytes(C, F, P_pad, Ny, nkx, sigma_k, single_pass=not args.separate_passes)
     hbm, hsrc = peaks()
     dom = max(stage_ms, key=stage_ms.get)
     ach = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
@@ -328,6 +341,7 @@ def run_ours(args, rank, world, local_rank):
                    "bin": w.bin, "P": rec.info["P"], "events_per_gpu": C, "e_per_frame": w.e_per_frame,
                    "precision": "FP32 FFT" if args.precision == "fp32" else "split-FP16 tcgen05 DFT (x) + FP32 FFT (y)",
                    "norm": "none", "sigma_K": sigma_k,
+                   "event_passes": 3 if args.separate_passes else 1,
                    "l2": "inputs larger than L2 (events 4 B x C = %.0f MB; G %.2f GB); no flush" %
                          (4 * C / 1e6, 8 * P_pad * Ny * nkx / 1e9),
                    "parallelism": f"replicas x{world} (independent datasets, no collective)"},

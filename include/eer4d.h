@@ -168,6 +168,13 @@ int com_dpc(const eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const
             int64_t* d_sums, float* d_com, float* d_phase, const int64_t* d_totals, double cx,
             double cy, double lam1, double lam2, void* d_scratch, uint32_t* d_status, void* stream);
 
+/* com_dpc from per-frame sums already formed (d_sums int64 [3][F], e.g. by
+ * ssb_accumulate_com): the same centre, COM maps and DPC phase, without a
+ * pass over the events.  Same outputs, scratch and errors as com_dpc. */
+int com_dpc_sums(const eer4d_plan* plan, const int64_t* d_sums, float* d_com, float* d_phase,
+                 const int64_t* d_totals, double cx, double cy, double lam1, double lam2,
+                 void* d_scratch, uint32_t* d_status, void* stream);
+
 /* ---- virtual detectors (Table 1: operations in O(C) on linear-index EER) ----
  * For every frame f the number of events in each of n_rings (1..EER4D_MAX_RINGS)
  * annuli about the pattern centre: ring j holds the raw pixels (x, y) with
@@ -224,6 +231,23 @@ int dpc_iterative(const eer4d_plan* plan, const float* d_com, double lam1, doubl
 int ssb_accumulate(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
                    uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
                    int is_last, uint32_t* d_status, void* stream);
+
+/* ---- a1 + a2 + a4 + a5 in one pass over the events ------------------------
+ * ssb_accumulate whose scatter pass also forms, for the frames
+ * [first_frame, first_frame + n_frames), the per-frame COM sums of com_dpc
+ * (Eq. 4): d_sums int64 [3][F] (Sx, Sy, N of the frame's in-range events,
+ * exact) and adds them to d_totals int64 [3] (the PACBED totals of
+ * eer_load_csr, for the centre; zero it before the first chunk).  Offsets and
+ * indices are checked as in eer_load_csr (EER4D_ST_OFFSETS, EER4D_ST_RANGE).
+ * A frame with more than 65535 events sets EER4D_ST_OVERFLOW (as in
+ * ssb_accumulate) and its sums then cover its first 65535 events.  Follow
+ * with com_dpc_sums for the COM maps and the DPC phase.  Same arguments,
+ * workspace and errors as ssb_accumulate otherwise; d_sums and d_totals must
+ * not be NULL. */
+int ssb_accumulate_com(eer4d_plan* plan, const uint32_t* d_idx, uint64_t n_idx,
+                       const uint64_t* d_off, uint64_t first_frame, uint64_t n_frames,
+                       void* d_counts, void* d_G, int is_last, int64_t* d_sums, int64_t* d_totals,
+                       uint32_t* d_status, void* stream);
 
 /* ---- a6 + a7: SSB trotter integration and phase image (Eq. 3) --------------
  * For each candidate c (d_aberr: double[n_cand][5] on the device, so a CUDA

@@ -6,7 +6,8 @@ C ABI of include/eer4d.h); this package is its Python binding.
 
 from . import _lib
 from ._lib import (  # noqa: F401  (C-ABI names)
-    Plan, Eer4dError, eer_load_csr, com_dpc, ssb_accumulate, ssb_reconstruct, ssb_grad,
+    Plan, Eer4dError, eer_load_csr, com_dpc, com_dpc_sums, ssb_accumulate, ssb_accumulate_com,
+    ssb_reconstruct, ssb_grad,
     ssb_variance_grad, ssb_trotter_counts, ssb_refocus_step, eer4d_set_stage_events,
     eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, FP32_STOCKHAM, NORM_NONE, NORM_AREA,
     ssb_reconstruct_batched, batched_scratch_bytes, MAX_SETS, eer_decode_rle,

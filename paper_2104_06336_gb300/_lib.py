@@ -26,7 +26,7 @@ NORM_NONE, NORM_AREA = 0, 1
 EXPORTS = [
     "eer4d_plan_create", "eer4d_plan_destroy", "eer4d_plan_info", "eer4d_workspace_bytes",
     "eer4d_status_code", "eer4d_strerror", "eer4d_last_error", "eer_load_csr", "com_dpc",
-    "ssb_accumulate", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
+    "ssb_accumulate", "ssb_accumulate_com", "com_dpc_sums", "ssb_reconstruct", "ssb_grad", "ssb_variance_grad", "ssb_trotter_counts",
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
     "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
     "virtual_detectors", "ssb_g_slices", "dpc_iterative", "eer4d_autotune", "eer4d_set_tuning",
@@ -112,6 +112,8 @@ def load(path: str | None = None):
         "eer_load_csr": (I32, [P, P, U64, P, U64, P, P, P, P]),
         "com_dpc": (I32, [P, P, U64, P, P, P, P, P, D, D, D, D, P, P, P]),
         "ssb_accumulate": (I32, [P, P, U64, P, U64, U64, P, P, I32, P, P]),
+        "ssb_accumulate_com": (I32, [P, P, U64, P, U64, U64, P, P, I32, P, P, P, P]),
+        "com_dpc_sums": (I32, [P, P, P, P, P, D, D, D, D, P, P, P]),
         "ssb_reconstruct": (I32, [P, P, P, I32, P, P, P, P, P]),
         "ssb_grad": (I32, [P, P, P, P, P, P, P, P]),
         "ssb_variance_grad": (I32, [P, P, P, P, P, P, P, P, P]),
@@ -264,6 +266,47 @@ def ssb_accumulate(plan: Plan, idx, off, first_frame: int, counts, G, is_last: b
                                  int(first_frame), off.numel() - 1, _ptr(counts, "counts"),
                                  _ptr(G, "G"), int(bool(is_last)), _ptr(status, "status"),
                                  _stream()), "ssb_accumulate")
+
+
+def ssb_accumulate_com(plan: Plan, idx, off, first_frame: int, counts, G, is_last: bool, sums,
+                       totals, status=None):
+    """ssb_accumulate that also forms the per-frame COM sums [3][F] of its
+    frames and adds them to totals [3] in the same pass over the events."""
+    _need(idx, 0, "idx", _U32)
+    _need(off, 8, "off", torch.int64)
+    _need(counts, plan.workspace_bytes(1)[0], "counts (workspace)")
+    _need(G, plan.G_bytes, "G")
+    if sums is None or totals is None:
+        raise ValueError("ssb_accumulate_com needs sums and totals")
+    _need(sums, 24 * plan.F, "sums", torch.int64)
+    _need(totals, 24, "totals", torch.int64)
+    _need(status, 16, "status")
+    _check(load().ssb_accumulate_com(plan.handle, _ptr(idx, "idx"), idx.numel(), _ptr(off, "off"),
+                                     int(first_frame), off.numel() - 1, _ptr(counts, "counts"),
+                                     _ptr(G, "G"), int(bool(is_last)), _ptr(sums, "sums"),
+                                     _ptr(totals, "totals"), _ptr(status, "status"), _stream()),
+           "ssb_accumulate_com")
+
+
+def com_dpc_sums(plan: Plan, sums, com, phase=None, totals=None, cx=0.0, cy=0.0, lam1=0.0,
+                 lam2=0.0, scratch=None, status=None):
+    """com_dpc from per-frame sums [3][F] already formed (ssb_accumulate_com)."""
+    F = plan.F
+    if sums is None:
+        raise ValueError("com_dpc_sums needs sums")
+    _need(sums, 24 * F, "sums", torch.int64)
+    _need(com, 8 * F, "com", torch.float32)
+    _need(phase, 4 * F, "phase", torch.float32)
+    _need(totals, 24, "totals", torch.int64)
+    if phase is not None:
+        if scratch is None:
+            raise ValueError("com_dpc_sums needs scratch (8 bytes per frame) for the phase")
+        _need(scratch, 8 * F, "scratch")
+    _need(status, 16, "status")
+    _check(load().com_dpc_sums(plan.handle, _ptr(sums, "sums"), _ptr(com, "com"),
+                               _ptr(phase, "phase"), _ptr(totals, "totals"), float(cx), float(cy),
+                               float(lam1), float(lam2), _ptr(scratch, "scratch"),
+                               _ptr(status, "status"), _stream()), "com_dpc_sums")
 
 
 def ssb_reconstruct(plan: Plan, G, aberr, scratch, phase=None, var=None, status=None):

@@ -398,9 +398,24 @@ int com_dpc(const eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const ui
   return cuda_fail(launch_idpc(p, z, d_phase, lam1, lam2, s));
 }
 
-int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
-                   uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G, int is_last,
-                   uint32_t* d_status, void* stream) {
+int com_dpc_sums(const eer4d_plan* p, const int64_t* d_sums, float* d_com, float* d_phase,
+                 const int64_t* d_totals, double cx, double cy, double lam1, double lam2,
+                 void* d_scratch, uint32_t* d_status, void* stream) {
+  (void)d_status;
+  if (!p || !d_sums || !d_com) return EER4D_EINVAL;
+  if (d_phase && !d_scratch) return EER4D_EINVAL;
+  if (!(lam1 >= 0.0) || !(lam2 >= 0.0)) return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* z = d_phase ? static_cast<float2*>(d_scratch) : nullptr;
+  int rc = cuda_fail(launch_com_from_sums(p, d_sums, d_com, z, d_totals, cx, cy, s));
+  if (rc != EER4D_OK || !d_phase) return rc;
+  return cuda_fail(launch_idpc(p, z, d_phase, lam1, lam2, s));
+}
+
+static int accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                      uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
+                      int is_last, int64_t* d_sums, int64_t* d_totals, uint32_t* d_status,
+                      void* stream) {
   if (!p || !d_off || (n_idx && !d_idx) || !d_counts || !d_G) return EER4D_EINVAL;
   const uint64_t F = (uint64_t)p->F;
   const uint64_t end = first_frame + n_frames;
@@ -414,7 +429,7 @@ int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
                                          al256(work_counts_bytes(p)));
   float2* G = static_cast<float2*>(d_G);
   int rc = cuda_fail(launch_scatter(p, d_idx, n_idx, d_off, first_frame, n_frames, counts,
-                                    d_status, s));
+                                    d_status, s, d_sums, d_totals));
   if (rc != EER4D_OK) return rc;
   const uint64_t Nx = p->g.scan_nx;
   if (dft2_fused_ok(p)) {  // both axes in one launch once every frame is in
@@ -438,6 +453,22 @@ int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
     p->next_frame = 0;
   }
   return rc;
+}
+
+int ssb_accumulate(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                   uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G, int is_last,
+                   uint32_t* d_status, void* stream) {
+  return accumulate(p, d_idx, n_idx, d_off, first_frame, n_frames, d_counts, d_G, is_last, nullptr,
+                    nullptr, d_status, stream);
+}
+
+int ssb_accumulate_com(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const uint64_t* d_off,
+                       uint64_t first_frame, uint64_t n_frames, void* d_counts, void* d_G,
+                       int is_last, int64_t* d_sums, int64_t* d_totals, uint32_t* d_status,
+                       void* stream) {
+  if (!d_sums || !d_totals) return EER4D_EINVAL;
+  return accumulate(p, d_idx, n_idx, d_off, first_frame, n_frames, d_counts, d_G, is_last, d_sums,
+                    d_totals, d_status, stream);
 }
 
 int ssb_reconstruct(const eer4d_plan* p, const void* d_G, const double* d_aberr, int n_cand,

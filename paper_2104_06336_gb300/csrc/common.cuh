@@ -160,9 +160,14 @@ cudaError_t launch_virtual_detectors(const eer4d_plan* p, const uint32_t* idx, u
 cudaError_t launch_rle_decode(const uint32_t* runs, uint64_t n, const uint64_t* off,
                               uint64_t n_frames, uint32_t* idx, uint32_t* st, cudaStream_t s);
 int scatter_tf_for(const eer4d_plan* p);
+// sums [3][F] and totals [3] non-NULL: the same pass forms the per-frame COM
+// sums of the frames [first, first + n) and adds them to totals
 cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                            const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
-                           uint32_t* st, cudaStream_t s);
+                           uint32_t* st, cudaStream_t s, int64_t* sums = nullptr,
+                           int64_t* totals = nullptr);
+cudaError_t launch_com_from_sums(const eer4d_plan* p, const int64_t* sums, float* com, float2* z,
+                                 const int64_t* totals, double cx, double cy, cudaStream_t s);
 cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, int y0, int y1,
                           cudaStream_t s);
 cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cudaStream_t s);

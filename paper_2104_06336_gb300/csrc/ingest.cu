@@ -100,6 +100,39 @@ constexpr int kComThreads = 256;
 // frames of at most this many events sum x and y in 32 bits (x, y < 32768)
 constexpr uint64_t kComFast = 131071;
 
+// The COM centre as an exact integer part and a float fraction (from double):
+// the PACBED centre of mass from the totals, or (cx, cy) when there are none.
+struct ComCentre {
+  long long ix, iy;
+  float fx, fy;
+};
+__device__ __forceinline__ ComCentre com_centre(const long long* totals, double cx, double cy) {
+  if (totals) {
+    const long long n = totals[2];
+    cx = n ? (double)totals[0] / (double)n : 0.0;
+    cy = n ? (double)totals[1] / (double)n : 0.0;
+  }
+  const double rx = rint(cx), ry = rint(cy);
+  ComCentre c;
+  c.ix = (long long)rx;
+  c.iy = (long long)ry;
+  c.fx = (float)(cx - rx);
+  c.fy = (float)(cy - ry);
+  return c;
+}
+// COM of one frame relative to the centre, (Sx - N round(cx)) / N - frac(cx)
+// in float32 (0 for an empty frame).
+__device__ __forceinline__ void com_of_frame(long long sx, long long sy, long long sn,
+                                             const ComCentre& c, float& ox, float& oy) {
+  ox = oy = 0.f;
+  if (sn) {
+    const long long dx = sx - sn * c.ix;
+    const long long dy = sy - sn * c.iy;
+    ox = (float)dx / (float)sn - c.fx;
+    oy = (float)dy / (float)sn - c.fy;
+  }
+}
+
 __global__ void __launch_bounds__(kComThreads, 8) k_com(const uint32_t* __restrict__ idx, uint64_t n_idx,
                                                      const uint64_t* __restrict__ off, uint32_t F,
                                                      uint32_t WH, DivMod dw,
@@ -107,20 +140,8 @@ __global__ void __launch_bounds__(kComThreads, 8) k_com(const uint32_t* __restri
                                                      double cx_h, double cy_h, float zscale,
                                                      long long* sums, float* com, float2* z,
                                                      uint32_t* st) {
-  __shared__ float s_cfx, s_cfy;
-  __shared__ long long s_cix, s_ciy;
-  if (threadIdx.x == 0) {
-    // centre: integer part (exact) + fractional part (float), from double
-    double cx = cx_h, cy = cy_h;
-    if (totals) {
-      const long long n = totals[2];
-      cx = n ? (double)totals[0] / (double)n : 0.0;
-      cy = n ? (double)totals[1] / (double)n : 0.0;
-    }
-    const double rx = rint(cx), ry = rint(cy);
-    s_cix = (long long)rx; s_ciy = (long long)ry;
-    s_cfx = (float)(cx - rx); s_cfy = (float)(cy - ry);
-  }
+  __shared__ ComCentre s_c;
+  if (threadIdx.x == 0) s_c = com_centre(totals, cx_h, cy_h);
   const uint32_t f = blockIdx.x * kComThreads + threadIdx.x;
   unsigned long long sx = 0, sy = 0, sn = 0;
   uint32_t drop = 0;
@@ -169,13 +190,8 @@ __global__ void __launch_bounds__(kComThreads, 8) k_com(const uint32_t* __restri
     sums[f] = (long long)sx;
     sums[F + f] = (long long)sy;
     sums[2 * (size_t)F + f] = (long long)sn;
-    float ox = 0.f, oy = 0.f;
-    if (sn) {
-      const long long dx = (long long)sx - (long long)sn * s_cix;
-      const long long dy = (long long)sy - (long long)sn * s_ciy;
-      ox = (float)dx / (float)sn - s_cfx;
-      oy = (float)dy / (float)sn - s_cfy;
-    }
+    float ox, oy;
+    com_of_frame((long long)sx, (long long)sy, (long long)sn, s_c, ox, oy);
     com[f] = ox;
     com[F + f] = oy;
     if (z) z[f] = make_float2(ox * zscale, oy * zscale);
@@ -185,6 +201,25 @@ __global__ void __launch_bounds__(kComThreads, 8) k_com(const uint32_t* __restri
     st_or(st, EER4D_ST_RANGE);
     st_add(st, 1, drop);
   }
+}
+
+// COM maps from per-frame sums [3][F] already formed (by the scatter pass of
+// ssb_accumulate_com): the same centre and arithmetic as k_com.
+__global__ void __launch_bounds__(kComThreads) k_com_from_sums(const long long* __restrict__ sums,
+                                                               uint32_t F,
+                                                               const long long* __restrict__ totals,
+                                                               double cx_h, double cy_h,
+                                                               float zscale, float* com, float2* z) {
+  __shared__ ComCentre s_c;
+  if (threadIdx.x == 0) s_c = com_centre(totals, cx_h, cy_h);
+  __syncthreads();
+  const uint32_t f = blockIdx.x * kComThreads + threadIdx.x;
+  if (f >= F) return;
+  float ox, oy;
+  com_of_frame(sums[f], sums[F + f], sums[2 * (size_t)F + f], s_c, ox, oy);
+  com[f] = ox;
+  com[F + f] = oy;
+  if (z) z[f] = make_float2(ox * zscale, oy * zscale);
 }
 
 // ---------------------------------------------------------------- a4 -------
@@ -206,13 +241,18 @@ constexpr int kMaxFrameEvents = 65535;
 #ifndef EER4D_SCATTER_MINB
 #define EER4D_SCATTER_MINB 2
 #endif
-__global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
+// SUMS: the same pass also forms each frame's COM sums (Sx, Sy, N over its
+// in-range events; Eq. 4) into sums[3][F] and adds them to totals[3] (the
+// PACBED centre), in the tiles of pixel chunk 0; events past the first
+// 65535 of a frame (EER4D_ST_OVERFLOW) are counted in neither.
+template <bool SUMS>
+__global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_scatter(
     const uint32_t* __restrict__ idx, uint64_t n_idx, const uint64_t* __restrict__ off,
     uint64_t first, uint64_t nfr, uint32_t W, uint32_t H, DivMod dw,
     const int16_t* __restrict__ lutp, const int16_t* __restrict__ lutx,
     const int16_t* __restrict__ luty, const int32_t* __restrict__ lut2, int pw, int ph, int P_pad,
     int TF, int PC, DivMod nch, uint32_t ntiles, int tab_smem, uint64_t NR, __half* counts,
-    uint32_t* st) {
+    long long* sums, unsigned long long* totals, uint64_t F, uint32_t* st) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_lo[128];  // event range of each tile frame
   __shared__ uint32_t s_n[128];
@@ -229,19 +269,20 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) ty[i] = luty[i];
     for (int i = threadIdx.x; i < pw * ph; i += blockDim.x) t2[i] = (int16_t)lut2[i];
   }
-  auto pixel = [&](uint32_t v) -> int {
+  // kept pixel of raw index v (< W*H); (x, y) are v's detector coordinates
+  // when the tables or SUMS needed them
+  auto pixel = [&](uint32_t v, uint32_t& x, uint32_t& y) -> int {
     if (tab_smem) {
-      uint32_t y, x;
       dw.divmod(v, y, x);
       const int u = tx[x], vv = ty[y];
       return (u | vv) < 0 ? -1 : t2[vv * pw + u];
     }
+    if (SUMS || !lutp) dw.divmod(v, y, x);
     if (lutp) return __ldg(lutp + v);
-    uint32_t y, x;
-    dw.divmod(v, y, x);
     const int u = __ldg(lutx + x), vv = __ldg(luty + y);
     return (u | vv) < 0 ? -1 : __ldg(lut2 + vv * pw + u);
   };
+  unsigned long long tsx = 0, tsy = 0, tsn = 0;  // lane 0: this warp's share of the totals
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   uint32_t drop = 0, over = 0;
   const uint64_t T0 = (first / TF) * TF;
@@ -286,6 +327,9 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
     for (int jg = j0 + warp; jg < j1; jg += 4 * nw) {
       uint64_t lo4[4];
       uint32_t n4[4], nmax = 0;
+      uint32_t fsx[SUMS ? 4 : 1], fsy[SUMS ? 4 : 1], fsn[SUMS ? 4 : 1];
+#pragma unroll
+      for (int f = 0; f < (SUMS ? 4 : 1); ++f) fsx[f] = fsy[f] = fsn[f] = 0u;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         const int j = jg + f * nw;
@@ -311,8 +355,31 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
             if (kk >= n4[f]) continue;
             const uint32_t e = v[2 * f + h];
             if (e >= WH) { ++drop; continue; }
-            const int pp = pixel(e) - p0;
+            uint32_t ex = 0u, ey = 0u;
+            const int pp = pixel(e, ex, ey) - p0;
+            if constexpr (SUMS) { fsx[f] += ex; fsy[f] += ey; fsn[f] += 1u; }
             if ((unsigned)pp < (unsigned)pc) atomicAdd(col + pp * TP, inc);
+          }
+        }
+      }
+      if constexpr (SUMS) {
+        // the four frames' sums (32-bit: < 65536 events of x, y < 65536), once per frame
+        if (p0 == 0) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const uint32_t a = __reduce_add_sync(0xffffffffu, fsx[f]);
+            const uint32_t b = __reduce_add_sync(0xffffffffu, fsy[f]);
+            const uint32_t c = __reduce_add_sync(0xffffffffu, fsn[f]);
+            const int j = jg + f * nw;
+            if (lane == 0 && j < j1) {
+              const uint64_t g = tf0 + j;  // frame of the dataset
+              sums[g] = a;
+              sums[F + g] = b;
+              sums[2 * F + g] = c;
+              tsx += a;
+              tsy += b;
+              tsn += c;
+            }
           }
         }
       }
@@ -360,6 +427,11 @@ __global__ void __launch_bounds__(kThreads, EER4D_SCATTER_MINB) k_scatter(
   if (lane == 0) {
     if (drop) { st_or(st, EER4D_ST_RANGE); st_add(st, 1, drop); }
     if (over) { st_or(st, EER4D_ST_OVERFLOW); st_add(st, 2, over); }
+    if (SUMS && tsn) {
+      atomicAdd(totals + 0, tsx);
+      atomicAdd(totals + 1, tsy);
+      atomicAdd(totals + 2, tsn);
+    }
   }
 }
 
@@ -425,13 +497,26 @@ cudaError_t launch_com(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
   return cudaGetLastError();
 }
 
+cudaError_t launch_com_from_sums(const eer4d_plan* p, const int64_t* sums, float* com, float2* z,
+                                 const int64_t* totals, double cx, double cy, cudaStream_t s) {
+  const uint32_t F = (uint32_t)p->F;
+  const float zscale = (float)(p->g.dalpha_raw_rad / p->g.lambda_A);
+  stage_begin(p, EER4D_STAGE_COM, s);
+  k_com_from_sums<<<(F + kComThreads - 1) / kComThreads, kComThreads, 0, s>>>(
+      reinterpret_cast<const long long*>(sums), F, reinterpret_cast<const long long*>(totals), cx,
+      cy, zscale, com, z);
+  count_launches(1);
+  stage_end(p, EER4D_STAGE_COM, s);
+  return cudaGetLastError();
+}
+
 int scatter_tf_for(const eer4d_plan* p) {
   return p->tune.scatter_tf > 0 ? p->tune.scatter_tf : scatter_tf(p->P_pad);
 }
 
 cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_idx,
                            const uint64_t* off, uint64_t first, uint64_t n, __half* counts,
-                           uint32_t* st, cudaStream_t s) {
+                           uint32_t* st, cudaStream_t s, int64_t* sums, int64_t* totals) {
   if (n == 0) return cudaSuccess;
   const int TF = scatter_tf_for(p);
   const int PC = scatter_pc(p->P_pad, TF);
@@ -443,7 +528,9 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   // table in global memory otherwise, or the three global tables without it)
   const int tab_smem = tabs <= kScatterTabBytes;
   const size_t sm = tile + (tab_smem ? (tabs + 15) / 16 * 16 : 0);
-  cudaError_t e = ensure_smem((const void*)k_scatter, sm);
+  const bool with_sums = sums != nullptr;
+  const void* kern = with_sums ? (const void*)k_scatter<true> : (const void*)k_scatter<false>;
+  cudaError_t e = ensure_smem(kern, sm);
   if (e != cudaSuccess) return e;
   const uint64_t T0 = (first / TF) * TF;
   const uint64_t tiles = (first + n - T0 + TF - 1) / TF * NCH;
@@ -453,17 +540,19 @@ cudaError_t launch_scatter(const eer4d_plan* p, const uint32_t* idx, uint64_t n_
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, kThreads, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, sm);
   if (occ < 1) return cudaErrorInvalidConfiguration;  // the tile does not fit shared memory
   const int cps = p->tune.scatter_ctas_per_sm > 0 && p->tune.scatter_ctas_per_sm < occ
                       ? p->tune.scatter_ctas_per_sm : occ;
   uint64_t grid = (uint64_t)nsm * cps;
   if (grid > tiles) grid = tiles;
   stage_begin(p, EER4D_STAGE_SCATTER, s);
-  k_scatter<<<(unsigned)grid, kThreads, sm, s>>>(
+  auto kl = with_sums ? k_scatter<true> : k_scatter<false>;
+  kl<<<(unsigned)grid, kThreads, sm, s>>>(
       idx, n_idx, off, first, n, W, H, p->dw, p->d_lutp, p->d_lutx, p->d_luty, p->d_lut2,
       (int)p->g.pw, (int)p->g.ph, p->P_pad, TF, PC, nch, (uint32_t)tiles, tab_smem, (uint64_t)p->cstride,
-      counts, st);
+      counts, reinterpret_cast<long long*>(sums), reinterpret_cast<unsigned long long*>(totals),
+      (uint64_t)p->F, st);
   count_launches(1);
   stage_end(p, EER4D_STAGE_SCATTER, s);
   return cudaGetLastError();
