@@ -311,6 +311,21 @@ __global__ void __launch_bounds__(kWarps * 32,
           gb[i] = ((mAny >> i) & 1u)
                       ? Gl[(size_t)(PACKED ? (int)(xv[i] & 0xffffu) : sp[xv[i]]) * P.Ny]
                       : make_float2(0.f, 0.f);
+        if (PACKED && !nyq_warp) {
+          // every list entry has a member among the warp's lanes, and a lane
+          // that is not a member of entry i holds G = 0 there, so its term is
+          // exactly 0: the entries run as independent straight-line chains
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const bool memM = (mM >> i) & 1u;
+            const int q = (int)(xv[i] >> 16);
+            const float2 g = gb[i];
+            const float2 gg = memM ? make_float2(g.x, -g.y) : g;
+            contrib(gg, memM ? Kmx : Kpx, memM ? Kmy : Kpy, skk[q], q, memM ? 0.f : 1.f, SP, SM, DP,
+                    DM);
+          }
+          return;
+        }
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
