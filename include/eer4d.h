@@ -220,7 +220,7 @@ int dpc_iterative(const eer4d_plan* plan, const float* d_com, double lam1, doubl
  * intermediate of the scan DFT:
  *  - FP32_FFT plans of square scans with side 128, 256, 512 or 1024: nothing
  *    until is_last; then one persistent launch does both axes through a ring
- *    of three pixel-group slabs kept in L2 and its task counters;
+ *    of four pixel-group slabs (the two in use kept in L2) and its task counters;
  *  - otherwise: the DFT along x of every scan row completed by this chunk,
  *    complex64 [scan_nx/2+1][scan_ny][P_pad]; with is_last the DFT along y.
  * Chunks must arrive in frame order starting at frame 0 (else EORDER).  With
