@@ -206,9 +206,9 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------ GPU arm --
 STAGE_BYTES_DOC = {
     "validate": "4 B/event + 8 B/frame",
-    "com": "4 B/event + 8 B/frame in; 40 B/frame out",
+    "com": "one pass: 24 B/frame of sums in, 16 B/frame out; three passes: 4 B/event + 8 B/frame in, 40 B/frame out",
     "dpc": "8 B/frame in + 4 B/frame out",
-    "scatter": "4 B/event + 8 B/frame in; 2 B x P_pad per frame out",
+    "scatter": "4 B/event + 8 B/frame in; 2 B x P_pad per frame out (+ 24 B/frame of COM sums in the one-pass step)",
     "dft_x": "2 B x P_pad per frame in; 8 B x P_pad x (Nx/2+1)/Nx per frame out",
     "dft_y": "8 B x P_pad x (Nx/2+1)/Nx per frame in and out (transposed out)",
     "trotter": "8 B per (pixel, K) pair of the trotter sets + 8 B per stored bin out",
