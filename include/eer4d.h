@@ -338,10 +338,23 @@ int ssb_reconstruct_batched(const eer4d_plan* const* h_plans, const void* const*
  * the array, which keeps the last call's contents (nothing in it needs to
  * start at zero); calls that overlap on the GPU race on it, so order them on
  * one stream.  The first call on each device looks up the array's device
- * address; make that first call before any stream capture. */
+ * address; make that first call before any stream capture.  The address is
+ * kept for the life of the process, so it assumes the device is not reset
+ * (cudaDeviceReset) while the library is in use. */
 #define EER4D_STATIC_SCRATCH_BYTES (8u << 20)
 int ssb_reconstruct_static(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
                            float* d_phase, double* d_var, uint32_t* d_status, void* stream);
+
+/* ---- split DFT factors of the tensor-core scan transform (Sec. IV) ------------
+ * Host only (needs no GPU): the factors the EER4D_SPLIT_FP16 scan DFT builds
+ * its tables from.  For k in [0, n_k), x in [0, n) and c in {0, 1}:
+ * w = cos(2 pi e / n) (c = 0) or -sin(2 pi e / n) (c = 1) with the exact
+ * integer phase index e = (k x) mod n, evaluated in double;
+ * h_hi[(k n + x) 2 + c] = bits of fp16(w) and h_lo[...] = bits of
+ * fp16(w - hi), so hi + lo carries about 22 significant bits of w.  h_hi and
+ * h_lo (caller-owned) hold 2 n n_k uint16 each.  EINVAL for n outside
+ * [1, 65536], n_k outside [1, n] or a NULL buffer. */
+int eer4d_dft_split_factors(int n, int n_k, uint16_t* h_hi, uint16_t* h_lo);
 
 /* ---- launch-shape autotuner (not part of the method) --------------------------
  * Tile and grid shapes of the three main kernels.  Zero means the built-in

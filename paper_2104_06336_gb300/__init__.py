@@ -12,7 +12,7 @@ from ._lib import (  # noqa: F401  (C-ABI names)
     eer4d_launch_count, status_code, FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, FP32_STOCKHAM, NORM_NONE, NORM_AREA,
     ssb_reconstruct_batched, batched_scratch_bytes, MAX_SETS, eer_decode_rle,
     virtual_detectors, MAX_RINGS, ssb_g_slices, MAX_SLICES, dpc_iterative, eer4d_autotune,
-    eer4d_set_tuning, eer4d_get_tuning, eer4d_selftest_wait,
+    eer4d_set_tuning, eer4d_get_tuning, eer4d_selftest_wait, eer4d_dft_split_factors,
 )
 from .pipeline import Reconstructor, reconstruct_batched, StreamedSteps  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401

@@ -30,7 +30,7 @@ EXPORTS = [
     "ssb_refocus_step", "eer4d_set_stage_events", "eer4d_launch_count", "ssb_reconstruct_static",
     "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
     "virtual_detectors", "ssb_g_slices", "dpc_iterative", "eer4d_autotune", "eer4d_set_tuning",
-    "eer4d_get_tuning", "eer4d_selftest_wait",
+    "eer4d_get_tuning", "eer4d_selftest_wait", "eer4d_dft_split_factors",
 ]
 MAX_SLICES = 64
 MAX_RINGS = 64
@@ -129,6 +129,7 @@ def load(path: str | None = None):
         "eer4d_autotune": (I32, [P, P, U64, P, P, P, P, P, P, P, C.POINTER(Tuning)]),
         "eer4d_set_tuning": (I32, [P, C.POINTER(Tuning)]),
         "eer4d_selftest_wait": (I32, [P, P, P]),
+        "eer4d_dft_split_factors": (I32, [I32, I32, P, P]),
         "eer4d_get_tuning": (I32, [P, C.POINTER(Tuning)]),
         "ssb_g_slices": (I32, [P, P, C.POINTER(C.c_int32), I32, P, P]),
         "virtual_detectors": (I32, [P, P, U64, P, U64, C.POINTER(D), I32, P, D, D, P, P, P, P]),
@@ -530,3 +531,14 @@ def eer4d_selftest_wait(scratch, status):
     _need(status, 16, "status")
     _check(load().eer4d_selftest_wait(_ptr(scratch, "scratch"), _ptr(status, "status"), _stream()),
            "eer4d_selftest_wait")
+
+
+def eer4d_dft_split_factors(n: int, n_k: int):
+    """The split hi + lo fp16 DFT factors of the tensor-core scan transform
+    (host only): two float16 arrays [n_k][n][2] (cos, -sin)."""
+    import numpy as np
+    hi = np.zeros((n_k, n, 2), dtype=np.uint16)
+    lo = np.zeros_like(hi)
+    _check(load().eer4d_dft_split_factors(n, n_k, C.c_void_p(hi.ctypes.data), C.c_void_p(lo.ctypes.data)),
+           "eer4d_dft_split_factors")
+    return hi.view(np.float16), lo.view(np.float16)

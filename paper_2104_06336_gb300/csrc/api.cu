@@ -112,6 +112,8 @@ constexpr size_t kTrotterListsMaxBytes = (size_t)512 << 20;
 
 }  // namespace
 
+int cuda_status(cudaError_t e) { return cuda_fail(e); }
+
 size_t work_counts_bytes(const eer4d_plan* p) { return (size_t)2 * p->P_pad * p->cstride; }
 size_t work_bytes(const eer4d_plan* p) {
   if (dft2_fused_ok(p)) return al256(work_counts_bytes(p)) + al256(dft2_ring_bytes(p)) + dft2_ctl_bytes(p);

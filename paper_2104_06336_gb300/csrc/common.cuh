@@ -104,6 +104,9 @@ struct eer4d_plan {
 void stage_begin(const eer4d_plan* p, int stage, cudaStream_t s);
 void stage_end(const eer4d_plan* p, int stage, cudaStream_t s);
 void count_launches(int n);
+// EER4D_OK for cudaSuccess; otherwise records the error text for
+// eer4d_last_error and returns EER4D_ECUDA.
+int cuda_status(cudaError_t e);
 // Raises a kernel's dynamic shared-memory limit to at least `bytes`; remembers
 // what it set so repeated launches (and graph captures) make no further call.
 cudaError_t ensure_smem(const void* kernel, size_t bytes);

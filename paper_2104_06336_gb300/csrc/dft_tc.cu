@@ -422,6 +422,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
 }  // namespace
 
+// Host: one DFT factor exp(-2 pi i k x / n), component c (0 = cos, 1 = -sin),
+// from the exact integer phase index (k x) mod n in double, split as
+// hi = fp16(w), lo = fp16(w - hi).
+static void dft_split(int n, long long k, long long x, int c, __half* hi, __half* lo) {
+  const double tp = 6.283185307179586476925286766559;
+  const long long e = (k * x) % n;
+  const double w = c ? -sin(tp * (double)e / n) : cos(tp * (double)e / n);
+  *hi = __float2half_rn((float)w);
+  *lo = __float2half_rn((float)(w - (double)__half2float(*hi)));
+}
+
+extern "C" int eer4d_dft_split_factors(int n, int n_k, uint16_t* h_hi, uint16_t* h_lo) {
+  if (n < 1 || n > 65536 || n_k < 1 || n_k > n || !h_hi || !h_lo) return EER4D_EINVAL;
+  for (int k = 0; k < n_k; ++k)
+    for (int x = 0; x < n; ++x)
+      for (int c = 0; c < 2; ++c) {
+        __half hi, lo;
+        dft_split(n, k, x, c, &hi, &lo);
+        const size_t o = ((size_t)k * n + x) * 2 + c;
+        h_hi[o] = __half_as_ushort(hi);
+        h_lo[o] = __half_as_ushort(lo);
+      }
+  return EER4D_OK;
+}
+
 // Host: the tile-blocked split DFT matrix for this plan's Nx.
 cudaError_t make_dftx_tc(eer4d_plan* p) {
   const int Nx = p->g.scan_nx, nkx = p->nkx;
@@ -429,7 +454,6 @@ cudaError_t make_dftx_tc(eer4d_plan* p) {
   const int NT = (2 * nkx + kN - 1) / kN;
   const size_t tile_elems = (size_t)kN * kK;
   std::vector<__half> hi((size_t)NT * KT * tile_elems), lo(hi.size());
-  const double tp = 6.283185307179586476925286766559;
   for (int nt = 0; nt < NT; ++nt)
     for (int kt = 0; kt < KT; ++kt) {
       __half* th = hi.data() + ((size_t)nt * KT + kt) * tile_elems;
@@ -437,13 +461,8 @@ cudaError_t make_dftx_tc(eer4d_plan* p) {
       for (int r = 0; r < kN; ++r)
         for (int k = 0; k < kK; ++k) {
           const int n = nt * kN + r, x = kt * kK + k, kx = n >> 1;
-          double w = 0.0;
-          if (x < Nx && kx < nkx) {
-            const long long e = ((long long)kx * x) % Nx;  // exact integer phase index
-            w = (n & 1) ? -sin(tp * (double)e / Nx) : cos(tp * (double)e / Nx);
-          }
-          const __half h = __float2half_rn((float)w);
-          const __half l = __float2half_rn((float)(w - (double)__half2float(h)));
+          __half h = __float2half_rn(0.f), l = h;
+          if (x < Nx && kx < nkx) dft_split(Nx, kx, x, n & 1, &h, &l);
           const size_t o = ((size_t)(r >> 3) * 1024 + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2;
           th[o] = h;
           tl[o] = l;

@@ -22,7 +22,10 @@
 //   them on one stream.
 // * The first call on each device looks up the array's device address with
 //   cudaGetSymbolAddress (with that device current); make that first call
-//   before any stream capture.
+//   before any stream capture.  The address is kept for the life of the
+//   process: it assumes the device's primary context is not reset
+//   (cudaDeviceReset) while the library is in use; after a reset the kept
+//   address is stale.
 #include <mutex>
 
 #include "common.cuh"
@@ -62,8 +65,8 @@ extern "C" int ssb_reconstruct_static(const eer4d_plan* p, const void* d_G, cons
   cudaError_t e = cudaGetDevice(&dev);
   void* scratch = nullptr;
   if (e == cudaSuccess) e = scratch_address(dev, &scratch);
-  if (e != cudaSuccess) return EER4D_ECUDA;
-  e = launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_FWD, scratch, nullptr,
-                     d_phase, d_var, nullptr, nullptr, d_status, (cudaStream_t)stream);
-  return e == cudaSuccess ? EER4D_OK : EER4D_ECUDA;
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_FWD,
+                                    scratch, nullptr, d_phase, d_var, nullptr, nullptr, d_status,
+                                    (cudaStream_t)stream));
 }

@@ -10,6 +10,13 @@ binned simulation pixel, so binning by ``bin`` recovers the simulated pixel
 exactly while the stored indices are genuine ``y*det_w + x`` raw linear indices
 (EER linear-index encoding, Sec. II and Fig. 1b).
 
+With ``scan_rot`` the scan axes are rotated against the object (and the
+detector, which shares the object's axes): frame (iy, ix) sits at
+R = R(scan_rot) (ix, iy) * step.  The window is taken at the integer part of R
+and the probe is shifted by the fractional part with a Fourier phase ramp
+(exact for the aperture-limited probe), so positions need no interpolation of
+the object.
+
 The generator runs with torch on CPU or CUDA.  It is deterministic for a given
 (workload, seed, device); CPU and CUDA draw different streams.  It holds no
 reconstruction arithmetic.
@@ -80,6 +87,41 @@ def _aperture_probe(w: Workload, device, cdtype):
     return A.to(cdtype), a.to(cdtype)
 
 
+def _rotated_positions(w: Workload, fr: torch.Tensor):
+    """Window corner (y, x) in object px (float64) of the frames ``fr`` of a
+    rotated scan, shifted so every window lies inside the object grid."""
+    c, s = math.cos(w.scan_rot), math.sin(w.scan_rot)
+    y0, _y1, x0, _x1 = w.scan_corners()
+    X = (fr % w.scan_nx).to(torch.float64) * w.step_px
+    Y = (fr // w.scan_nx).to(torch.float64) * w.step_px
+    return s * X + c * Y - y0 + 1.0, c * X - s * Y - x0 + 1.0
+
+
+def _shifted_probes(A: torch.Tensor, fy: torch.Tensor, fx: torch.Tensor) -> torch.Tensor:
+    """Centred real-space probes a(r - f) for fractional shifts f = (fy, fx)
+    [n] in px: the spectrum times exp(-2 pi i k.f / P), k the signed
+    frequency index."""
+    P = A.shape[-1]
+    k = torch.fft.fftfreq(P, d=1.0 / P, device=A.device, dtype=torch.float64)
+    ramp = torch.exp(-2j * math.pi * (fy[:, None, None] * k[None, :, None]
+                                      + fx[:, None, None] * k[None, None, :]) / P)
+    A0 = torch.fft.ifftshift(A).to(torch.complex128)
+    a = torch.fft.fftshift(torch.fft.ifft2(A0[None] * ramp), dim=(-2, -1))
+    return a.to(A.dtype)
+
+
+def _fourier_sample(phi: torch.Tensor, y: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """phi (periodic on its grid) at real positions (y, x) by its Fourier
+    series."""
+    H, W = phi.shape
+    Phi = torch.fft.fft2(phi) / (H * W)
+    ky = torch.fft.fftfreq(H, device=phi.device, dtype=torch.float64)
+    kx = torch.fft.fftfreq(W, device=phi.device, dtype=torch.float64)
+    Ey = torch.exp(2j * math.pi * y[:, None] * ky[None, :])
+    Ex = torch.exp(2j * math.pi * x[:, None] * kx[None, :])
+    return ((Ey @ Phi) * Ex).sum(dim=1).real
+
+
 def object_phase(w: Workload, gen: torch.Generator, device) -> torch.Tensor:
     """Gaussian-filtered (sigma in sim px, periodic) N(0,1) noise, zero mean,
     scaled to ``phase_std``."""
@@ -113,8 +155,9 @@ def generate(w: Workload, device: str | torch.device = "cpu", *, seed: int | Non
     gobj = torch.Generator(device=device).manual_seed(seed * 7919 + 1)
     phi = object_phase(w, gobj, device) if phase is None else phase.to(device=device, dtype=torch.float64)
     T = torch.exp(1j * phi).to(cdtype)
-    _A, a = _aperture_probe(w, device, cdtype)
+    A, a = _aperture_probe(w, device, cdtype)
     P, Ny, Nx, s = w.sim_px, w.scan_ny, w.scan_nx, w.step_px
+    rotated = w.scan_rot != 0.0
     F = Ny * Nx
     f0, f1 = (0, F) if frames is None else frames
     if chunk is None:
@@ -128,13 +171,21 @@ def generate(w: Workload, device: str | torch.device = "cpu", *, seed: int | Non
     for cs in range(c0, f1, chunk):
         ce = min(cs + chunk, F)
         fr = torch.arange(cs, ce, device=device)
-        yy, xx = fr // Nx, fr % Nx
-        rows = (yy[:, None] * s + ar[None, :])
-        cols = (xx[:, None] * s + ar[None, :])
+        if rotated:
+            ry, rx = _rotated_positions(w, fr)
+            iy, ix = torch.floor(ry), torch.floor(rx)
+            probe = _shifted_probes(A, ry - iy, rx - ix)
+            rows = iy.to(torch.int64)[:, None] + ar[None, :]
+            cols = ix.to(torch.int64)[:, None] + ar[None, :]
+        else:
+            yy, xx = fr // Nx, fr % Nx
+            rows = (yy[:, None] * s + ar[None, :])
+            cols = (xx[:, None] * s + ar[None, :])
+            probe = a[None]
         if w.periodic:
             rows, cols = rows % w.obj_h, cols % w.obj_w
         win = T[rows[:, :, None], cols[:, None, :]]                    # [n][P][P]
-        psi = torch.fft.fftshift(torch.fft.fft2(a[None] * win), dim=(-2, -1))
+        psi = torch.fft.fftshift(torch.fft.fft2(probe * win), dim=(-2, -1))
         I = (psi.real ** 2 + psi.imag ** 2).to(torch.float64)
         I = I / I.sum(dim=(-2, -1), keepdim=True)
         gcnt.manual_seed(seed * 104729 + cs // chunk)
@@ -172,8 +223,12 @@ def generate(w: Workload, device: str | torch.device = "cpu", *, seed: int | Non
     off = torch.zeros(n_all.numel() + 1, dtype=torch.int64, device=device)
     off[1:] = torch.cumsum(n_all, 0)
     c = P // 2
-    gy = (torch.arange(Ny, device=device) * s + c) % w.obj_h
-    gx = (torch.arange(Nx, device=device) * s + c) % w.obj_w
-    phi_scan = phi[gy[:, None], gx[None, :]]
+    if rotated:
+        ry, rx = _rotated_positions(w, torch.arange(F, device=device))
+        phi_scan = _fourier_sample(phi, ry + c, rx + c).reshape(Ny, Nx)
+    else:
+        gy = (torch.arange(Ny, device=device) * s + c) % w.obj_h
+        gx = (torch.arange(Nx, device=device) * s + c) % w.obj_w
+        phi_scan = phi[gy[:, None], gx[None, :]]
     inten = torch.cat(inten_parts) if want_intensity else None
     return EventData(idx=idx, off=off, phi_scan=phi_scan, intensity=inten)

@@ -53,6 +53,8 @@ class Workload:
     crop_margin: float = 0.0   # crop radius = k0 + margin (binned px)
     aberr: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)  # C1, C12a, C12b, C3 (A), rot (rad)
     periodic: bool = False     # object periodic over the scan (N*step)
+    scan_rot: float = 0.0      # scan axes rotated by this angle (rad, counter-clockwise in the
+                               # detector's (x, y)) against the object and detector axes
 
     # derived quantities -------------------------------------------------
     @property
@@ -74,6 +76,18 @@ class Workload:
     @property
     def n_frames(self) -> int:
         return self.scan_ny * self.scan_nx
+
+    def scan_corners(self):
+        """Offsets (y, x) in sim px of the scan's extreme positions: frame (iy, ix)
+        sits at R = R(scan_rot) (ix step, iy step), R(t) = [[cos t, -sin t],
+        [sin t, cos t]] acting on (x, y)."""
+        c, s = math.cos(self.scan_rot), math.sin(self.scan_rot)
+        X = (self.scan_nx - 1) * self.step_px
+        Y = (self.scan_ny - 1) * self.step_px
+        pts = [(0.0, 0.0), (X, 0.0), (0.0, Y), (X, Y)]
+        xs = [c * x - s * y for x, y in pts]
+        ys = [s * x + c * y for x, y in pts]
+        return min(ys), max(ys), min(xs), max(xs)
 
     @property
     def crop_x0(self) -> int:
@@ -125,6 +139,7 @@ def workload(cfg: int, **over) -> Workload:
                      obj_h=_obj(1024, 2, 96), obj_w=_obj(1024, 2, 96), **_BASE)
     else:
         raise ValueError(f"unknown workload {cfg}")
+    user_obj = "obj_h" in over
     if over:
         if ("scan_ny" in over or "scan_nx" in over or "step_px" in over) and "obj_h" not in over:
             ny = over.get("scan_ny", w.scan_ny)
@@ -133,7 +148,13 @@ def workload(cfg: int, **over) -> Workload:
             over = dict(over, obj_h=_obj(ny, st, w.sim_px), obj_w=_obj(nx, st, w.sim_px))
         w = replace(w, **over)
     if w.periodic:
+        if w.scan_rot != 0.0:
+            raise ValueError("a rotated scan does not tile a periodic object")
         w = replace(w, obj_h=w.scan_ny * w.step_px, obj_w=w.scan_nx * w.step_px)
+    elif w.scan_rot != 0.0 and not user_obj:
+        y0, y1, x0, x1 = w.scan_corners()
+        w = replace(w, obj_h=int(math.ceil(y1 - y0)) + w.sim_px + 2,
+                    obj_w=int(math.ceil(x1 - x0)) + w.sim_px + 2)
     return w
 
 

@@ -85,3 +85,31 @@ def test_valid_geometries_pass_host_validation(lib):
         assert rc in (0, -6), (cfg, rc)
         if rc == 0:
             lib.eer4d_plan_destroy(h)
+
+
+@pytest.mark.parametrize("n", [16, 96, 1024])
+def test_split_dft_factors_within_bound(lib, n):
+    """The tensor-core scan DFT's split factors (Sec. IV: the transform as a
+    matrix product; the factors W = exp(-2 pi i k x / n) are split hi + lo
+    fp16): every hi + lo is within 2^-22 |w| plus half the fp16 subnormal
+    spacing (2^-25) of the FP64 value, hi is the fp16 nearest w, and the phase
+    index is the exact integer (k x) mod n (checked at k x far beyond n)."""
+    import numpy as np
+    from paper_2104_06336_gb300._lib import eer4d_dft_split_factors
+    n_k = n // 2 + 1
+    hi, lo = eer4d_dft_split_factors(n, n_k)
+    k = np.arange(n_k)[:, None]
+    x = np.arange(n)[None, :]
+    e = (k * x) % n
+    w = np.stack([np.cos(2 * np.pi * e / n), -np.sin(2 * np.pi * e / n)], axis=-1)
+    h = hi.astype(np.float64)
+    err = np.abs(h + lo.astype(np.float64) - w)
+    assert np.all(err <= 2.0 ** -22 * np.abs(w) + 2.0 ** -25), err.max()
+    # hi is the fp16 nearest w (up to the double -> float -> half rounding of a tie)
+    assert np.all(np.abs(h - w) <= np.abs(np.spacing(h.astype(np.float16)).astype(np.float64)) * 0.5
+                  + 2.0 ** -25)
+    # exact symmetric values
+    assert np.all(h[:, 0, 0] == 1.0) and np.all(lo[:, 0, :] == 0.0)
+    if n % 4 == 0:
+        assert h[1, n // 4, 0] == 0.0 or abs(h[1, n // 4, 0]) < 2.0 ** -24
+        assert h[1, n // 4, 1] == -1.0

@@ -10,7 +10,8 @@ import pytest
 
 import oracle as orc
 import oracle.eer4d_oracle as core
-from test_oracle_pins import _weak_phase_case, _lens
+from test_oracle_pins import (_lens, _weak_phase_case, test_scan_rotation_direction_from_forward_model,
+                              test_spherical_aberration_term_from_forward_model)
 
 
 def _weak_err(**kw):
@@ -97,3 +98,30 @@ def test_wrong_phase_image_part_fails(monkeypatch):
     monkeypatch.setattr(core, "np", FakeNP())
     _, r = _weak_err()
     assert abs(r) < 0.5
+
+
+def test_doubled_spherical_coefficient_fails(monkeypatch):
+    """C3 w^4/2 in place of C3 w^4/4 (and its derivative) fails the C3 pin."""
+    real = core.chi_turns
+    monkeypatch.setattr(core, "chi_turns",
+                        lambda qx, qy, ab, g: real(qx, qy, ab, g) + real(qx, qy, (0.0, 0.0, 0.0, ab[3]), g))
+    with pytest.raises(AssertionError):
+        test_spherical_aberration_term_from_forward_model()
+
+
+def test_spherical_term_sign_fails(monkeypatch):
+    real = core.chi_turns
+    monkeypatch.setattr(core, "chi_turns",
+                        lambda qx, qy, ab, g: real(qx, qy, (ab[0], ab[1], ab[2], -ab[3]), g))
+    with pytest.raises(AssertionError):
+        test_spherical_aberration_term_from_forward_model()
+
+
+def test_rotation_sign_flipped_consistently_fails(monkeypatch):
+    """K' = R(-rot) K in every place the oracle forms K' (the float32 mask
+    and the double phase) fails the rotation pin."""
+    r32, r64 = core.kprime_f32, core.kprime_f64
+    monkeypatch.setattr(core, "kprime_f32", lambda geom, rot: r32(geom, -rot))
+    monkeypatch.setattr(core, "kprime_f64", lambda geom, rot: r64(geom, -rot))
+    with pytest.raises(AssertionError):
+        test_scan_rotation_direction_from_forward_model()

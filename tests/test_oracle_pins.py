@@ -455,6 +455,34 @@ def test_ssb_unnormalised_transfer_is_trotter_count():
     assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) <= 0.02
 
 
+def _poisson_ssb_corr(e_per_frame, shuffle=False):
+    w = synth.workload(1, periodic=True, phase_std=0.1, sigma_px=2.0, e_per_frame=e_per_frame)
+    geom = synth.geometry(w)
+    d = synth.generate(w)
+    idx, off = d.numpy()
+    counts = orc.densify(idx, off, geom)
+    if shuffle:  # frames at the wrong scan positions: no object information left
+        counts = counts[:, np.random.default_rng(0).permutation(counts.shape[1])]
+    G = orc.g_function(counts, geom)
+    phi, _ = orc.ssb_phase(G, geom, (0, 0, 0, 0, 0), "none")
+    _, nK = orc.ssb_spectrum(G, geom, (0, 0, 0, 0, 0), "none")
+    ref = np.fft.ifft2(np.fft.fft2(d.phi_scan.numpy()) * nK).real
+    return np.corrcoef(phi.ravel(), ref.ravel())[0, 1]
+
+
+def test_ssb_on_poisson_events_follows_shot_noise():
+    """SSB from Poisson electron events (the tiny workload's 30 e-/frame, and
+    ten times that): the image correlates with the trotter-filtered object far
+    above the shuffled-frame control, and the gain with dose follows shot
+    noise: for signal plus independent noise of variance proportional to
+    1/dose, r(d2) = 1 / sqrt(1 + (1/r(d1)^2 - 1) d1/d2)."""
+    r30, r300 = _poisson_ssb_corr(30.0), _poisson_ssb_corr(300.0)
+    ctrl = _poisson_ssb_corr(30.0, shuffle=True)
+    assert r30 > 0.15 and r30 > 5 * abs(ctrl), (r30, ctrl)
+    pred = 1.0 / math.sqrt(1.0 + (1.0 / r30 ** 2 - 1.0) * 0.1)
+    assert abs(r300 - pred) <= 0.06, (r30, r300, pred)
+
+
 def test_aberration_correction_sign():
     """Reading of Eq. 3 under numpy's sign: reconstructing with the true
     aberrations beats no correction and the conjugate correction."""
@@ -465,6 +493,51 @@ def test_aberration_correction_sign():
         r[name] = np.corrcoef(phi.ravel(), ref.ravel())[0, 1]
     assert r["true"] > 0.98
     assert r["true"] > r["zero"] + 0.2 and r["true"] > r["conj"] + 0.2
+
+
+def test_spherical_aberration_term_from_forward_model():
+    """The C3 term of the aberration function (Sec. IV, A(k) of Eq. 3): the
+    forward model (its own chi, written separately) makes data with C3 = 50 um
+    and C1 = 4 nm; reconstructing with the true C3 reaches the weak-phase
+    error floor, while 0.75 C3, 1.25 C3, 0 and 2 C3 are far off.  A wrong
+    coefficient, power or sign of the C3 term moves the minimum."""
+    ab = (40.0, 0.0, 0.0, 5.0e5, 0.0)
+    err = {}
+    for s in (0.0, 0.75, 1.0, 1.25, 2.0):
+        ra = (ab[0], 0.0, 0.0, s * ab[3], 0.0)
+        phi, ref, _ = _weak_phase_case(0.01, aberr=ab, recon_aberr=ra)
+        err[s] = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert err[1.0] <= 0.01, err
+    assert min(err[0.75], err[1.25]) >= 0.1, err
+    assert min(err[0.0], err[2.0]) >= 1.0, err
+
+
+def _rotated_scan_case(theta, ab=(200.0, 0.0, 0.0, 0.0, 0.0), n=32):
+    w = synth.workload(1, scan_ny=n, scan_nx=n, phase_std=0.01, sigma_px=2.0, aberr=ab,
+                       scan_rot=theta)
+    geom = synth.geometry(w)
+    d = synth.generate(w, want_intensity=True)
+    G = orc.g_function(orc.bin_crop_dense(d.intensity.numpy(), geom), geom)
+    return G, geom, d.phi_scan.numpy()
+
+
+def test_scan_rotation_direction_from_forward_model():
+    """Scan rotation (K' = R(rot) K, counter-clockwise in the detector's x, y):
+    the forward model places frame (iy, ix) at R(theta) (ix, iy) step in the
+    object frame.  With defocus present the aberration phase depends on the
+    direction of K', so only the right rotation recovers the object:
+    rot = theta beats -theta, 0 and theta +- 0.1 by correlation with the true
+    phase at the probe positions."""
+    th = 0.35
+    ab = (200.0, 0.0, 0.0, 0.0, 0.0)
+    G, geom, truth = _rotated_scan_case(th, ab)
+    r = {}
+    for rot in (th, -th, 0.0, th - 0.1, th + 0.1):
+        phi, _ = orc.ssb_phase(G, geom, ab[:4] + (rot,), "area")
+        r[rot] = np.corrcoef(phi.ravel(), truth.ravel())[0, 1]
+    assert r[th] > 0.75, r
+    assert r[th] > r[-th] + 0.5 and r[th] > r[0.0] + 0.2, r
+    assert r[th] > max(r[th - 0.1], r[th + 0.1]) + 0.01, r
 
 
 # --------------------------------------------------------------- adjoint ---
