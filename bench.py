@@ -56,6 +56,9 @@ def parse():
                     help="also time the 16-dataset batching workload: one batched launch vs one call per dataset")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split"],
                     help="scan DFT form: FP32 FFT or split-FP16 tensor-core DFT along x")
+    ap.add_argument("--no-refocus-fit", action="store_true",
+                    help="skip the refocus comparison on the 25 mrad optics (adjoint fit from zero vs "
+                         "a 64-candidate grid search)")
     return ap.parse_args()
 
 
@@ -478,9 +481,74 @@ def run_ours(args, rank, world, local_rank):
         }
         rec.check()
 
+    # ---- refocus accuracy: adjoint fit from zero vs grid search --------------
+    # the differentiation workload's optics (25 mrad, 1941 bright-field pixels,
+    # true C1 = 8 nm, C12 = 3 nm at 30 deg, C3 = 1 um) on the 1024x1024 scan:
+    # the plain arm is a 64-candidate defocus grid (-20..20 nm, the other
+    # aberrations 0) in one batched launch; the adjoint arm replays the
+    # captured Adam step (ssb_refocus_step_adam) from all aberrations zero.
+    if args.refocus_steps > 0 and not args.no_refocus_fit and rank == 0:
+        del rec
+        torch.cuda.empty_cache()
+        w3 = synth.workload(3, scan_ny=w.scan_ny, scan_nx=w.scan_nx)
+        d3 = synth.generate(w3, dev)
+        r3 = P.Reconstructor(synth.geometry(w3), n_cand=64, device=dev)
+        r3.load(d3.idx, d3.off)
+        del d3
+        true = torch.tensor(w3.aberr, dtype=torch.float64)
+        grid = torch.zeros(64, 5, dtype=torch.float64, device=dev)
+        grid[:, 0] = torch.linspace(-200.0, 200.0, 64, dtype=torch.float64, device=dev)
+        vg = torch.empty(64, dtype=torch.float64, device=dev)
+
+        def grid_search():
+            P.ssb_reconstruct(r3.plan, r3.G, grid, r3.scratch, None, vg, status=r3.status)
+
+        grid_search()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grid_search()
+        b.record()
+        torch.cuda.synchronize()
+        t_grid = a.elapsed_time(b)
+        best = grid[int(torch.argmax(vg))].cpu()
+        err_grid = (best - true)[:4].abs().tolist()
+        fg = P.refocus.RefocusGraph(r3, [0.0] * 5, adam=[0.05, 0.05, 0.05, 0.05, 0.0])
+        n_fit = 200
+        traj = []
+        for k in range(n_fit):
+            fg.replay()
+            if (k + 1) % 10 == 0:
+                traj.append((k + 1, (fg.theta.cpu() - true)[:4].abs().tolist()))
+        fg.reset()
+        torch.cuda.synchronize()
+        a.record()
+        fg.replay(n_fit)
+        b.record()
+        torch.cuda.synchronize()
+        t_fit = a.elapsed_time(b)
+        err_fit = (fg.theta.cpu() - true)[:4].abs().tolist()
+        # replays until the fit is at least as close as the grid on C1 (and
+        # fits C12a, C12b and C3, which the defocus grid leaves at 0)
+        reach = next((k for k, e in traj if e[0] <= err_grid[0]), None)
+        r3.check()
+        out["refocus_fit"] = {
+            "workload": w3.name.replace("512x512", f"{w.scan_ny}x{w.scan_nx}"),
+            "true": [float(v) for v in w3.aberr[:4]],
+            "grid_search": {"candidates": 64, "what": "C1 in -20..20 nm, others 0, one batched launch",
+                            "ms": t_grid, "abs_err": err_grid},
+            "adjoint_fit": {"steps": n_fit, "what": "graph-replayed Adam steps from all aberrations 0",
+                            "ms": t_fit, "ms_per_step": t_fit / n_fit, "abs_err": err_fit,
+                            "steps_to_grid_C1_accuracy": reach,
+                            "ms_to_grid_C1_accuracy": None if reach is None else reach * t_fit / n_fit},
+            "abs_err_units": "A (C1, C12a, C12b, C3)",
+        }
+        del r3, fg
+        torch.cuda.empty_cache()
+
     # ---- uneven batches: 16 datasets in one launch vs one call each ----------
     if args.batching:
-        del rec
+        rec = None
         torch.cuda.empty_cache()
         ws = synth.batching_datasets()
         recs = []

@@ -99,6 +99,8 @@ typedef struct eer4d_info {
   int32_t n_rows;   /* detector rows holding bright-field pixels */
   int32_t nkx;      /* scan_nx/2 + 1 stored K_x columns of G */
   int32_t trotter_list_max;  /* upper bound of |K(K)| + |K(-K)| */
+  int32_t p_begin, p_end;    /* kept pixels [p_begin, p_end) of the full plan's numbering
+                                this plan owns (0, P for a plan of eer4d_plan_create) */
 } eer4d_info;
 
 typedef struct eer4d_plan eer4d_plan;
@@ -292,6 +294,19 @@ int ssb_refocus_step(const eer4d_plan* plan, const void* d_G, double* d_aberr, c
                      void* d_scratch, float* d_phase, double* d_var, double* d_grad,
                      uint32_t* d_status, void* stream);
 
+/* The same refocus step with an Adam update instead of a fixed step, so a
+ * captured graph of it converges from any start (for example all
+ * aberrations 0) without tuning a step per parameter.  In scaled parameters
+ * x_j = theta_j / scale_j: m1 = 0.9 m1 + 0.1 g, m2 = 0.999 m2 + 0.001 g^2
+ * (g = dV/dtheta_j scale_j), theta_j += scale_j lr_j m1^ / (sqrt(m2^) + 1e-12)
+ * with the bias-corrected moments m^ of step t.  d_rate double[10] = lr[5]
+ * (lr_j = 0 holds theta_j), scale[5]; d_state double[11] = m1[5], m2[5], t,
+ * zeroed by the caller before the first step and carried from step to
+ * step. */
+int ssb_refocus_step_adam(const eer4d_plan* plan, const void* d_G, double* d_aberr,
+                          const double* d_rate, double* d_state, void* d_scratch, float* d_phase,
+                          double* d_var, double* d_grad, uint32_t* d_status, void* stream);
+
 /* ---- G-function viewer (Fig. 2, middle panel) -------------------------------
  * G(k, K) at n (1..EER4D_MAX_SLICES) scan frequencies, for judging residual
  * aberrations: h_bins (host) holds n pairs (m_y, m_x) of DFT bin indices
@@ -322,6 +337,53 @@ int eer4d_batched_scratch_bytes(const eer4d_plan* const* h_plans, int n_sets, si
 int ssb_reconstruct_batched(const eer4d_plan* const* h_plans, const void* const* h_G, int n_sets,
                             const double* d_aberr, void* d_scratch, float* const* h_phase,
                             double* d_var, uint32_t* d_status, void* stream);
+
+/* ---- pixel shards: one dataset over several GPUs (Sec. IV) --------------------
+ * G(k, K) is a transform of each detector pixel's image on its own, and the
+ * trotter sum of Eq. 3 is a sum over pixels k, so the pixels of one dataset
+ * can be split between GPUs that then exchange only the partial spectra
+ * ("no inter-device transfers" of the data itself, Sec. IV).
+ *
+ * eer4d_shard_range (host only, needs no GPU): shard `shard` of `n_shards`
+ * (1..EER4D_MAX_SHARDS) of P kept pixels is [*h_begin, *h_end) =
+ * [floor(P shard / n), floor(P (shard + 1) / n)).
+ *
+ * eer4d_plan_create_shard: the plan eer4d_plan_create would make, restricted
+ * to that shard of its kept pixels (numbered row-major, v outer), renumbered
+ * from 0.  Its ssb_accumulate reads every event and keeps only its own pixels
+ * (other pixels' events are dropped like events outside the crop, with no
+ * status bit); its counts, G and trotter lists cover its pixels only.
+ * EINVAL when the shard holds no bright-field pixel (with the default
+ * bright-field crop every kept pixel is bright-field).  COM and DPC do not
+ * depend on the pixels: any plan computes them for the whole frame.
+ *
+ * ssb_spectrum_partial: this shard's share of the spectrum of ssb_reconstruct
+ * for n_cand candidates (as there, all of one rotation): d_H complex64
+ * [n_cand][scan_ny][scan_nx/2+1] = N_R (S_g(b) - conj S_g(-b)) / (2 i) for
+ * the stored bins b = (m_y, m_x <= scan_nx/2), S_g the sum of Eq. 3 over this
+ * plan's bright-field pixels, and d_g0 double[2] = (sum of G(k, 0) over them,
+ * their number).  Shares of all shards add up (element-wise sums of d_H and
+ * of d_g0, e.g. one all-reduce) to those of the whole pixel set.  Plans with
+ * EER4D_NORM_AREA return EINVAL (the per-bin set sizes would need their own
+ * exchange).  d_scratch as for ssb_reconstruct with n_cand candidates.
+ *
+ * ssb_image_from_spectrum: from summed shares (d_H, d_g0 as above, every
+ * shard's added), phi_c = Im(IFFT2(S)) N_R / Gbar0 with Gbar0 = d_g0[0] /
+ * d_g0[1] (phi = 0 when d_g0[0] is 0), written to d_phase float [n_cand][F]
+ * (nullable), and the variance to d_var double [n_cand] (nullable); equal to
+ * ssb_reconstruct on an unsharded plan up to rounding.  Any plan of the
+ * dataset may be passed; d_H is read only.  d_scratch as for ssb_reconstruct
+ * with n_cand candidates. */
+#define EER4D_MAX_SHARDS 64
+int eer4d_shard_range(int P, int shard, int n_shards, int* h_begin, int* h_end);
+int eer4d_plan_create_shard(const eer4d_geom* h_geom, int precision, int norm, int shard,
+                            int n_shards, eer4d_plan** out);
+int ssb_spectrum_partial(const eer4d_plan* plan, const void* d_G, const double* d_aberr,
+                         int n_cand, void* d_scratch, void* d_H, double* d_g0, uint32_t* d_status,
+                         void* stream);
+int ssb_image_from_spectrum(const eer4d_plan* plan, const void* d_H, const double* d_g0,
+                            int n_cand, void* d_scratch, float* d_phase, double* d_var,
+                            void* stream);
 
 /* ---- reconstruction without scratch allocation --------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

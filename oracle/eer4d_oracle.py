@@ -46,7 +46,7 @@ __all__ = [
     "bin_crop_dense", "com_sums", "com_sums_dense",
     "pacbed", "pacbed_centre", "com_maps", "idpc", "g_function", "gbar0", "chi_turns",
     "kprime_f32", "kprime_f64", "trotter_mask", "ssb_spectrum", "ssb_phase", "ssb_grad",
-    "variance", "ssb_value_and_grad_var", "fftfreq_index",
+    "variance", "ssb_value_and_grad_var", "fftfreq_index", "ssb_phase_from_events",
 ]
 
 TWO_PI = 2.0 * math.pi
@@ -432,13 +432,17 @@ def trotter_mask(kx_p, ky_p, KX, KY, k0sq):
 # --------------------------------------------------------------------------
 # SSB (Eq. 2, set K, Eq. 3) and the phase image
 # --------------------------------------------------------------------------
-def ssb_spectrum(G, geom, aberr, norm="none", mask_rot=None):
+def ssb_spectrum(G, geom, aberr, norm="none", mask_rot=None, pixels=None):
     """S(K) = sum_{p in K(K)} G(p, K) exp(-i (chi(k_p) - chi(k_p - K'))).
 
     norm = "none" (Eq. 3 as printed) or "area" (divide by |K(K)|, 0 when
     empty).  The mask uses rotation ``mask_rot`` (default: aberr[4]); the
-    aberration phase always uses aberr[4].  Returns S [Ny][Nx] and |K(K)|."""
+    aberration phase always uses aberr[4].  ``pixels`` (default: every kept
+    pixel, in order) names the kept pixel of each row of G; the sum then runs
+    over the bright-field pixels among them only.  Returns S [Ny][Nx] and
+    |K(K)| (both over those pixels)."""
     pt = pixel_table(geom)
+    rows = np.arange(pt["P"]) if pixels is None else np.asarray(pixels, dtype=np.int64)
     rot = float(aberr[4])
     mrot = rot if mask_rot is None else float(mask_rot)
     KXf, KYf = kprime_f32(geom, mrot)
@@ -447,7 +451,7 @@ def ssb_spectrum(G, geom, aberr, norm="none", mask_rot=None):
     Ny, Nx = geom["scan_ny"], geom["scan_nx"]
     S = np.zeros((Ny, Nx), dtype=np.complex128)
     nK = np.zeros((Ny, Nx), dtype=np.int64)
-    for p in range(pt["P"]):
+    for i, p in enumerate(rows):
         if not pt["bf"][p]:
             continue
         kx, ky = pt["kx"][p], pt["ky"][p]
@@ -455,7 +459,7 @@ def ssb_spectrum(G, geom, aberr, norm="none", mask_rot=None):
         if not member.any():
             continue
         psi = TWO_PI * (chi_turns(kx, ky, aberr, geom) - chi_turns(kx - KX, ky - KY, aberr, geom))
-        S += np.where(member, G[p] * np.exp(-1j * psi), 0.0)
+        S += np.where(member, G[i] * np.exp(-1j * psi), 0.0)
         nK += member
     if norm == "area":
         S = np.where(nK > 0, S / np.maximum(nK, 1), 0.0)
@@ -470,6 +474,40 @@ def ssb_phase(G, geom, aberr, norm="none", mask_rot=None):
     g0 = gbar0(G, geom)
     NR = geom["scan_ny"] * geom["scan_nx"]
     scale = NR / g0 if g0 != 0 else 0.0
+    phi = scale * np.fft.ifft2(S).imag
+    return phi, variance(phi)
+
+
+def ssb_phase_from_events(idx, off, geom, aberr, norm="none", chunk=16):
+    """phi and V of ssb_phase for scans whose full G does not fit in memory:
+    the bright-field pixels are taken chunk by chunk, each chunk's count rows
+    densified from the events, transformed over the scan and its trotter
+    terms added to S(K) (the same sums as ssb_spectrum, grouped by pixel);
+    Gbar0 collects G(k, 0) of the same pixels."""
+    pt = pixel_table(geom)
+    Ny, Nx = geom["scan_ny"], geom["scan_nx"]
+    F = Ny * Nx
+    p_ev, f_ev = event_pixels(idx, off, geom)
+    bf = np.flatnonzero(pt["bf"])
+    S = np.zeros((Ny, Nx), dtype=np.complex128)
+    nK = np.zeros((Ny, Nx), dtype=np.int64)
+    g0 = 0.0
+    for c0 in range(0, len(bf), chunk):
+        pix = bf[c0:c0 + chunk]
+        lo, hi = int(pix[0]), int(pix[-1]) + 1
+        sel = (p_ev >= lo) & (p_ev < hi)
+        rows = np.bincount((p_ev[sel] - lo) * F + f_ev[sel], minlength=(hi - lo) * F).reshape(hi - lo, F)
+        G = g_function(rows[pix - lo], geom)
+        s, n = ssb_spectrum(G, geom, aberr, "none", pixels=pix)
+        S += s
+        nK += n
+        g0 += float(np.sum(G[:, 0, 0].real))
+    if norm == "area":
+        S = np.where(nK > 0, S / np.maximum(nK, 1), 0.0)
+    elif norm != "none":
+        raise ValueError(norm)
+    gbar = g0 / len(bf) if len(bf) else 0.0
+    scale = F / gbar if gbar != 0 else 0.0
     phi = scale * np.fft.ifft2(S).imag
     return phi, variance(phi)
 

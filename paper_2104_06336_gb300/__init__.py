@@ -13,11 +13,14 @@ from ._lib import (  # noqa: F401  (C-ABI names)
     ssb_reconstruct_batched, batched_scratch_bytes, MAX_SETS, eer_decode_rle,
     virtual_detectors, MAX_RINGS, ssb_g_slices, MAX_SLICES, dpc_iterative, eer4d_autotune,
     eer4d_set_tuning, eer4d_get_tuning, eer4d_selftest_wait, eer4d_dft_split_factors,
+    eer4d_shard_range, ssb_spectrum_partial, ssb_image_from_spectrum, MAX_SHARDS,
+    ssb_refocus_step_adam,
 )
 from .pipeline import Reconstructor, reconstruct_batched, StreamedSteps  # noqa: F401
 from .autograd import SSBPhase, ssb_phase  # noqa: F401
 from . import refocus  # noqa: F401
 from . import tuning  # noqa: F401
+from . import sharding  # noqa: F401
 
 
 def build(force: bool = False) -> str:

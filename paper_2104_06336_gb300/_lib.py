@@ -31,7 +31,10 @@ EXPORTS = [
     "eer4d_batched_scratch_bytes", "ssb_reconstruct_batched", "eer_decode_rle",
     "virtual_detectors", "ssb_g_slices", "dpc_iterative", "eer4d_autotune", "eer4d_set_tuning",
     "eer4d_get_tuning", "eer4d_selftest_wait", "eer4d_dft_split_factors",
+    "eer4d_shard_range", "eer4d_plan_create_shard", "ssb_spectrum_partial", "ssb_image_from_spectrum",
+    "ssb_refocus_step_adam",
 ]
+MAX_SHARDS = 64
 MAX_SLICES = 64
 MAX_RINGS = 64
 MAX_SETS = 32
@@ -75,7 +78,8 @@ class Tuning(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("P", C.c_int32), ("P_pad", C.c_int32), ("P_bf", C.c_int32), ("n_rows", C.c_int32),
-                ("nkx", C.c_int32), ("trotter_list_max", C.c_int32)]
+                ("nkx", C.c_int32), ("trotter_list_max", C.c_int32), ("p_begin", C.c_int32),
+                ("p_end", C.c_int32)]
 
 
 _lib = None
@@ -119,6 +123,7 @@ def load(path: str | None = None):
         "ssb_variance_grad": (I32, [P, P, P, P, P, P, P, P, P]),
         "ssb_trotter_counts": (I32, [P, P, P, P, P]),
         "ssb_refocus_step": (I32, [P, P, P, P, P, P, P, P, P, P]),
+        "ssb_refocus_step_adam": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
         "eer4d_set_stage_events": (I32, [P, P, P]),
         "eer4d_launch_count": (C.c_uint64, []),
         "ssb_reconstruct_static": (I32, [P, P, P, P, P, P, P]),
@@ -130,6 +135,10 @@ def load(path: str | None = None):
         "eer4d_set_tuning": (I32, [P, C.POINTER(Tuning)]),
         "eer4d_selftest_wait": (I32, [P, P, P]),
         "eer4d_dft_split_factors": (I32, [I32, I32, P, P]),
+        "eer4d_shard_range": (I32, [I32, I32, I32, C.POINTER(I32), C.POINTER(I32)]),
+        "eer4d_plan_create_shard": (I32, [C.POINTER(Geom), I32, I32, I32, I32, C.POINTER(C.c_void_p)]),
+        "ssb_spectrum_partial": (I32, [P, P, P, I32, P, P, P, P, P]),
+        "ssb_image_from_spectrum": (I32, [P, P, P, I32, P, P, P, P]),
         "eer4d_get_tuning": (I32, [P, C.POINTER(Tuning)]),
         "ssb_g_slices": (I32, [P, P, C.POINTER(C.c_int32), I32, P, P]),
         "virtual_detectors": (I32, [P, P, U64, P, U64, C.POINTER(D), I32, P, D, D, P, P, P, P]),
@@ -186,11 +195,17 @@ class Plan:
     """An eer4d_plan on the current CUDA device (geometry dict with the field
     names of eer4d_geom)."""
 
-    def __init__(self, geom: dict, precision: int = FP32_FFT, norm: int = NORM_NONE):
+    def __init__(self, geom: dict, precision: int = FP32_FFT, norm: int = NORM_NONE,
+                 shard: tuple[int, int] | None = None):
         lib = load()
         g = Geom(**{k: geom[k] for k, _ in Geom._fields_})
         h = C.c_void_p()
-        _check(lib.eer4d_plan_create(C.byref(g), precision, norm, C.byref(h)), "eer4d_plan_create")
+        if shard is None:
+            _check(lib.eer4d_plan_create(C.byref(g), precision, norm, C.byref(h)), "eer4d_plan_create")
+        else:
+            _check(lib.eer4d_plan_create_shard(C.byref(g), precision, norm, int(shard[0]), int(shard[1]),
+                                               C.byref(h)), "eer4d_plan_create_shard")
+        self.shard = None if shard is None else (int(shard[0]), int(shard[1]))
         self._h = h
         self.geom = dict(geom)
         self.precision = precision
@@ -198,6 +213,7 @@ class Plan:
         info = Info()
         _check(lib.eer4d_plan_info(h, C.byref(info)), "eer4d_plan_info")
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
+        self.Ny = int(geom["scan_ny"])
         self.F = int(geom["scan_ny"]) * int(geom["scan_nx"])
         self.WH = int(geom["det_w"]) * int(geom["det_h"])
         self.G_bytes = 8 * self.info["nkx"] * self.info["P_pad"] * int(geom["scan_ny"])
@@ -374,6 +390,26 @@ def ssb_refocus_step(plan: Plan, G, aberr, step, scratch, var, grad, phase=None,
            "ssb_refocus_step")
 
 
+def ssb_refocus_step_adam(plan: Plan, G, aberr, rate, state, scratch, var, grad, phase=None,
+                          status=None):
+    """ssb_refocus_step with a device-side Adam update (rate: lr[5] + scale[5];
+    state: m1[5], m2[5], t, zeroed before the first step)."""
+    _need(G, plan.G_bytes, "G")
+    _need(aberr, 40, "aberr", torch.float64)
+    _need(rate, 80, "rate", torch.float64)
+    _need(state, 88, "state", torch.float64)
+    _need(scratch, plan.workspace_bytes(1)[2], "scratch")
+    _need(var, 8, "var", torch.float64)
+    _need(grad, 40, "grad", torch.float64)
+    _need(phase, 4 * plan.F, "phase", torch.float32)
+    _need(status, 16, "status")
+    _check(load().ssb_refocus_step_adam(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
+                                        _ptr(rate, "rate"), _ptr(state, "state"),
+                                        _ptr(scratch, "scratch"), _ptr(phase, "phase"),
+                                        _ptr(var, "var"), _ptr(grad, "grad"),
+                                        _ptr(status, "status"), _stream()), "ssb_refocus_step_adam")
+
+
 def eer4d_set_stage_events(plan: Plan, starts=None, stops=None):
     """starts/stops: lists of len(STAGES) torch.cuda.Event (or None) or None to clear."""
     if starts is None:
@@ -400,6 +436,43 @@ def ssb_reconstruct_static(plan: Plan, G, aberr, phase=None, var=None, status=No
     _check(load().ssb_reconstruct_static(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"),
                                          _ptr(phase, "phase"), _ptr(var, "var"),
                                          _ptr(status, "status"), _stream()), "ssb_reconstruct_static")
+
+
+def eer4d_shard_range(P: int, shard: int, n_shards: int) -> tuple[int, int]:
+    """Kept pixels [begin, end) of shard `shard` of `n_shards` (host only)."""
+    b, e = C.c_int(), C.c_int()
+    _check(load().eer4d_shard_range(int(P), int(shard), int(n_shards), C.byref(b), C.byref(e)),
+           "eer4d_shard_range")
+    return b.value, e.value
+
+
+def ssb_spectrum_partial(plan: Plan, G, aberr, scratch, H, g0, status=None):
+    """This plan's share of the spectrum: H complex64 [n][Ny][Nx/2+1] (as
+    float32 pairs or complex64) and g0 float64 [2]; see the header."""
+    n = aberr.numel() // 5
+    if n < 1 or aberr.numel() != 5 * n:
+        raise ValueError("aberr holds [n][5] float64 values")
+    _need(aberr, 40 * n, "aberr", torch.float64)
+    _need(G, plan.G_bytes, "G")
+    _need(scratch, plan.workspace_bytes(n)[2], "scratch")
+    _need(H, 8 * n * plan.Ny * plan.info["nkx"], "H", (torch.float32, torch.complex64))
+    _need(g0, 16, "g0", torch.float64)
+    _need(status, 16, "status")
+    _check(load().ssb_spectrum_partial(plan.handle, _ptr(G, "G"), _ptr(aberr, "aberr"), n,
+                                       _ptr(scratch, "scratch"), _ptr(H, "H"), _ptr(g0, "g0"),
+                                       _ptr(status, "status"), _stream()), "ssb_spectrum_partial")
+
+
+def ssb_image_from_spectrum(plan: Plan, H, g0, n_cand: int, scratch, phase=None, var=None):
+    """Phase images and variances from the summed shares of every shard."""
+    _need(H, 8 * n_cand * plan.Ny * plan.info["nkx"], "H", (torch.float32, torch.complex64))
+    _need(g0, 16, "g0", torch.float64)
+    _need(scratch, plan.workspace_bytes(n_cand)[2], "scratch")
+    _need(phase, 4 * n_cand * plan.F, "phase", torch.float32)
+    _need(var, 8 * n_cand, "var", torch.float64)
+    _check(load().ssb_image_from_spectrum(plan.handle, _ptr(H, "H"), _ptr(g0, "g0"), int(n_cand),
+                                          _ptr(scratch, "scratch"), _ptr(phase, "phase"),
+                                          _ptr(var, "var"), _stream()), "ssb_image_from_spectrum")
 
 
 def _handles(plans):

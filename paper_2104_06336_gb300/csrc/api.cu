@@ -160,7 +160,31 @@ int eer4d_set_stage_events(eer4d_plan* p, void* const* ev_start, void* const* ev
 
 const char* eer4d_last_error(void) { return g_last_error; }
 
+int eer4d_shard_range(int P, int shard, int n_shards, int* h_begin, int* h_end) {
+  if (P < 1 || n_shards < 1 || n_shards > EER4D_MAX_SHARDS || shard < 0 || shard >= n_shards ||
+      !h_begin || !h_end)
+    return EER4D_EINVAL;
+  *h_begin = (int)((long long)P * shard / n_shards);
+  *h_end = (int)((long long)P * (shard + 1) / n_shards);
+  return EER4D_OK;
+}
+
+static int create_plan(const eer4d_geom* h_geom, int precision, int norm, int shard, int n_shards,
+                       eer4d_plan** out);
+
 int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_plan** out) {
+  return create_plan(h_geom, precision, norm, 0, 1, out);
+}
+
+int eer4d_plan_create_shard(const eer4d_geom* h_geom, int precision, int norm, int shard,
+                            int n_shards, eer4d_plan** out) {
+  if (n_shards < 1 || n_shards > EER4D_MAX_SHARDS || shard < 0 || shard >= n_shards)
+    return EER4D_EINVAL;
+  return create_plan(h_geom, precision, norm, shard, n_shards, out);
+}
+
+static int create_plan(const eer4d_geom* h_geom, int precision, int norm, int shard, int n_shards,
+                       eer4d_plan** out) {
   if (!out) return EER4D_EINVAL;
   *out = nullptr;
   if (!geom_ok(h_geom)) return EER4D_EINVAL;
@@ -183,19 +207,34 @@ int eer4d_plan_create(const eer4d_geom* h_geom, int precision, int norm, eer4d_p
   p->dw.init(g.det_w);
 
   // kept pixels (|k| < crop, double) numbered row-major; bright-field
-  // |k|^2 < k0^2 in float32
+  // |k|^2 < k0^2 in float32.  A shard plan keeps the range [p_begin, p_end)
+  // of that numbering, renumbered from 0.
+  const double crop2 = g.crop_px * g.crop_px;
+  int P_all = 0;
+  for (uint32_t v = 0; v < g.ph; ++v)
+    for (uint32_t u = 0; u < g.pw; ++u) {
+      const int kx = (int)u - (int)g.dc_u, ky = (int)v - (int)g.dc_v;
+      if ((double)(kx * kx + ky * ky) < crop2) ++P_all;
+    }
+  if (P_all == 0) { free_plan(p); return EER4D_EINVAL; }
+  if (eer4d_shard_range(P_all, shard, n_shards, &p->p_begin, &p->p_end) != EER4D_OK ||
+      p->p_end <= p->p_begin) {
+    free_plan(p);
+    return EER4D_EINVAL;
+  }
+  p->shard = shard;
+  p->n_shards = n_shards;
   std::vector<int32_t> lut2((size_t)g.pw * g.ph, -1);
   std::vector<short2> pix;
   std::vector<int4> rows;
-  const double crop2 = g.crop_px * g.crop_px;
   const float k0sq = (float)(g.k0_px * g.k0_px);
-  int P_bf = 0;
+  int P_bf = 0, gi = -1;
   for (uint32_t v = 0; v < g.ph; ++v) {
     const int ky = (int)v - (int)g.dc_v;
     int lo = 1, hi = 0, plo = -1;
     for (uint32_t u = 0; u < g.pw; ++u) {
       const int kx = (int)u - (int)g.dc_u;
-      if ((double)(kx * kx + ky * ky) < crop2) {
+      if ((double)(kx * kx + ky * ky) < crop2 && ++gi >= p->p_begin && gi < p->p_end) {
         const int idx = (int)pix.size();
         lut2[(size_t)v * g.pw + u] = idx;
         pix.push_back(make_short2((short)kx, (short)ky));
@@ -297,6 +336,8 @@ int eer4d_plan_info(const eer4d_plan* p, eer4d_info* info) {
   info->n_rows = p->n_rows;
   info->nkx = p->nkx;
   info->trotter_list_max = 2 * p->P_bf;
+  info->p_begin = p->p_begin;
+  info->p_end = p->p_end;
   return EER4D_OK;
 }
 
@@ -482,6 +523,24 @@ int ssb_reconstruct(const eer4d_plan* p, const void* d_G, const double* d_aberr,
                                   (cudaStream_t)stream));
 }
 
+int ssb_spectrum_partial(const eer4d_plan* p, const void* d_G, const double* d_aberr, int n_cand,
+                         void* d_scratch, void* d_H, double* d_g0, uint32_t* d_status,
+                         void* stream) {
+  if (!p || !d_G || !d_aberr || !d_scratch || !d_H || !d_g0 || n_cand < 1 || n_cand > 1024)
+    return EER4D_EINVAL;
+  if (p->norm != EER4D_NORM_NONE) return EER4D_EINVAL;
+  return cuda_fail(launch_trotter_partial(p, static_cast<const float2*>(d_G), d_aberr, n_cand,
+                                          d_scratch, static_cast<float2*>(d_H), d_g0, d_status,
+                                          (cudaStream_t)stream));
+}
+
+int ssb_image_from_spectrum(const eer4d_plan* p, const void* d_H, const double* d_g0, int n_cand,
+                            void* d_scratch, float* d_phase, double* d_var, void* stream) {
+  if (!p || !d_H || !d_g0 || !d_scratch || n_cand < 1 || n_cand > 1024) return EER4D_EINVAL;
+  return cuda_fail(launch_image_from_spectrum(p, static_cast<const float2*>(d_H), d_g0, n_cand,
+                                              d_scratch, d_phase, d_var, (cudaStream_t)stream));
+}
+
 int ssb_grad(const eer4d_plan* p, const void* d_G, const double* d_aberr, const float* d_grad_phase,
              double* d_grad, void* d_scratch, uint32_t* d_status, void* stream) {
   if (!p || !d_G || !d_aberr || !d_grad_phase || !d_grad || !d_scratch) return EER4D_EINVAL;
@@ -512,6 +571,18 @@ int ssb_refocus_step(const eer4d_plan* p, const void* d_G, double* d_aberr, cons
                                     d_scratch, nullptr, d_phase, d_var, d_grad, nullptr, d_status, s));
   if (rc != EER4D_OK) return rc;
   return cuda_fail(launch_ascent(d_aberr, d_step, d_grad, s));
+}
+
+int ssb_refocus_step_adam(const eer4d_plan* p, const void* d_G, double* d_aberr, const double* d_rate,
+                          double* d_state, void* d_scratch, float* d_phase, double* d_var,
+                          double* d_grad, uint32_t* d_status, void* stream) {
+  if (!p || !d_G || !d_aberr || !d_rate || !d_state || !d_scratch || !d_var || !d_grad)
+    return EER4D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_fail(launch_trotter(p, static_cast<const float2*>(d_G), d_aberr, 1, TROT_VARGRAD,
+                                    d_scratch, nullptr, d_phase, d_var, d_grad, nullptr, d_status, s));
+  if (rc != EER4D_OK) return rc;
+  return cuda_fail(launch_adam(d_aberr, d_rate, d_state, d_grad, s));
 }
 
 static bool same_detector(const eer4d_plan* a, const eer4d_plan* b) {

@@ -65,6 +65,9 @@ struct eer4d_plan {
   eer4d_geom g;
   int precision, norm;
   int P, P_pad, P_bf, n_rows, nkx, list_max;
+  // pixel shard: this plan owns the kept pixels [p_begin, p_end) of the full
+  // plan's numbering (shard of n_shards; 0 of 1 for an ordinary plan)
+  int shard, n_shards, p_begin, p_end;
   int F;
   long long cstride;         // row stride (elements) of the fp16 counts [P_pad][cstride]
   DivMod dw;                 // division by det_w
@@ -206,6 +209,8 @@ cudaError_t launch_r2c_image(const eer4d_plan* p, const float* g, float2* W, cud
 // trotter modes
 enum { TROT_FWD = 0, TROT_GRAD = 1, TROT_VARGRAD = 2, TROT_COUNT = 3 };
 cudaError_t launch_ascent(double* theta, const double* step, const double* grad, cudaStream_t s);
+cudaError_t launch_adam(double* theta, const double* rate, double* state, const double* grad,
+                        cudaStream_t s);
 size_t trotter_batched_scratch_bytes(const eer4d_plan* const* plans, int n);
 size_t trotter_lists_bytes(const eer4d_plan* p);
 cudaError_t build_trotter_lists(eer4d_plan* p);
@@ -213,6 +218,14 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
                                    const double* aberr, void* scratch, float* const* phase,
                                    double* var, uint32_t* st, cudaStream_t s);
 size_t trotter_scratch_bytes(const eer4d_plan* p, int n_cand, int mode);
+// pixel shards: this plan's share of H (scale N_R, no Gbar0) and of
+// (sum G(k, 0), bright-field count); the image from summed shares
+cudaError_t launch_trotter_partial(const eer4d_plan* p, const float2* G, const double* aberr,
+                                   int n_cand, void* scratch, float2* H_out, double* g0_out,
+                                   uint32_t* st, cudaStream_t s);
+cudaError_t launch_image_from_spectrum(const eer4d_plan* p, const float2* H_in, const double* g0,
+                                       int n_cand, void* scratch, float* phase_out, double* var_out,
+                                       cudaStream_t s);
 cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* aberr, int n_cand,
                            int mode, void* scratch, const float2* W, float* phase_out,
                            double* var_out, double* grad_out, int32_t* count_out, uint32_t* st,

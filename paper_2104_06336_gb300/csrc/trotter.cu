@@ -667,9 +667,65 @@ __global__ void k_variance_final(const double* __restrict__ part, int nblk, doub
   if (threadIdx.x == 0) var[c] = red[0] / (NR * NR);
 }
 
+// Pixel shard: (sum of G(k, 0) over this plan's bright-field pixels, their
+// number) and the trotter scale N_R (the Gbar0 division waits for the sum
+// over every shard).
+__global__ void k_gbar_part(const float2* __restrict__ G, const int32_t* __restrict__ bfp, int P_bf,
+                            int Ny, double NR, double* g0_out, double* gscale) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < P_bf; q += blockDim.x) s += (double)G[(size_t)bfp[q] * Ny].x;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    g0_out[0] = red[0];
+    g0_out[1] = (double)P_bf;
+    gscale[0] = 0.0;
+    gscale[1] = NR;
+  }
+}
+
+// H = H_in / Gbar0, Gbar0 = g0[0] / g0[1] (H = 0 when g0[0] is 0)
+__global__ void k_scale_spectrum(const float2* __restrict__ Hin, const double* __restrict__ g0,
+                                 size_t n, float2* H) {
+  const double f = g0[0] != 0.0 ? g0[1] / g0[0] : 0.0;
+  const float ff = (float)f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = Hin[i];
+    H[i] = make_float2(v.x * ff, v.y * ff);
+  }
+}
+
 __global__ void k_ascent(double* theta, const double* step, const double* grad) {
   const int j = threadIdx.x;
   if (j < 5) theta[j] += step[j] * grad[j];
+}
+
+// Adam ascent on V in scaled parameters x_j = theta_j / scale_j (moments of
+// dV/dx_j = dV/dtheta_j scale_j; beta1 0.9, beta2 0.999, eps 1e-12):
+// theta_j += scale_j lr_j mhat_j / (sqrt(vhat_j) + eps).  rate = lr[5],
+// scale[5]; state = m1[5], m2[5], step count.  lr_j = 0 holds theta_j.
+__global__ void k_adam(double* theta, const double* rate, double* state, const double* grad) {
+  const int j = threadIdx.x;
+  const double t = state[10] + 1.0;
+  if (j < 5) {
+    const double sc = rate[5 + j];
+    const double g = grad[j] * sc;
+    const double m1 = 0.9 * state[j] + 0.1 * g;
+    const double m2 = 0.999 * state[5 + j] + 0.001 * g * g;
+    state[j] = m1;
+    state[5 + j] = m2;
+    const double mh = m1 / (1.0 - pow(0.9, t));
+    const double vh = m2 / (1.0 - pow(0.999, t));
+    if (rate[j] != 0.0) theta[j] += sc * rate[j] * mh / (sqrt(vh) + 1e-12);
+  }
+  __syncthreads();  // every lane has read the old count
+  if (j == 0) state[10] = t;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -731,10 +787,45 @@ cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
   return cudaGetLastError();
 }
 
+TrotParams trot_params(const eer4d_plan* p, int n_cand) {
+  TrotParams tp;
+  tp.Ny = p->g.scan_ny; tp.Nx = p->g.scan_nx; tp.nkx = p->nkx; tp.P_pad = p->P_pad;
+  tp.P_bf = p->P_bf;
+  tp.kpm_x = (float)p->g.kpm_x; tp.kpm_y = (float)p->g.kpm_y;
+  tp.k0sq = (float)(p->g.k0_px * p->g.k0_px);
+  tp.norm = p->norm; tp.n_cand = n_cand; tp.NR = (float)p->F;
+  return tp;
+}
+
+// variance (nullable) and the C2R phase image (nullable) of H [nc][Ny][nkx]
+cudaError_t image_stage(const eer4d_plan* p, const float2* H, int nc, double* vpart,
+                        float* phase_out, double* var_out, cudaStream_t s) {
+  cudaError_t e;
+  stage_begin(p, EER4D_STAGE_IMAGE, s);
+  if (var_out) {
+    k_variance_partial<<<dim3(kVarBlocks, nc), 256, 0, s>>>(H, p->g.scan_ny, p->nkx, p->g.scan_nx,
+                                                             vpart);
+    k_variance_final<<<nc, 128, 0, s>>>(vpart, kVarBlocks, (double)p->F, var_out);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (phase_out && (e = launch_c2r_image(p, const_cast<float2*>(H), phase_out, nc, s)) != cudaSuccess)
+    return e;
+  stage_end(p, EER4D_STAGE_IMAGE, s);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_ascent(double* theta, const double* step, const double* grad, cudaStream_t s) {
   k_ascent<<<1, 32, 0, s>>>(theta, step, grad);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(double* theta, const double* rate, double* state, const double* grad,
+                        cudaStream_t s) {
+  k_adam<<<1, 32, 0, s>>>(theta, rate, state, grad);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -767,12 +858,7 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  TrotParams tp;
-  tp.Ny = p->g.scan_ny; tp.Nx = p->g.scan_nx; tp.nkx = p->nkx; tp.P_pad = p->P_pad;
-  tp.P_bf = p->P_bf;
-  tp.kpm_x = (float)p->g.kpm_x; tp.kpm_y = (float)p->g.kpm_y;
-  tp.k0sq = (float)(p->g.k0_px * p->g.k0_px);
-  tp.norm = p->norm; tp.n_cand = n_cand; tp.NR = (float)p->F;
+  const TrotParams tp = trot_params(p, n_cand);
   int nblk = 1;
   switch (mode) {
     case TROT_FWD:
@@ -799,18 +885,51 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   }
   stage_end(p, EER4D_STAGE_TROTTER, s);
   if (mode == TROT_COUNT || mode == TROT_GRAD) return cudaSuccess;
-  const int nc = mode == TROT_FWD ? n_cand : 1;
-  stage_begin(p, EER4D_STAGE_IMAGE, s);
-  if (var_out) {
-    k_variance_partial<<<dim3(kVarBlocks, nc), 256, 0, s>>>(H, p->g.scan_ny, p->nkx, p->g.scan_nx,
-                                                             vpart);
-    k_variance_final<<<nc, 128, 0, s>>>(vpart, kVarBlocks, (double)p->F, var_out);
-    count_launches(2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (phase_out && (e = launch_c2r_image(p, H, phase_out, nc, s)) != cudaSuccess) return e;
-  stage_end(p, EER4D_STAGE_IMAGE, s);
+  return image_stage(p, H, mode == TROT_FWD ? n_cand : 1, vpart, phase_out, var_out, s);
+}
+
+cudaError_t launch_trotter_partial(const eer4d_plan* p, const float2* G, const double* aberr,
+                                   int n_cand, void* scratch, float2* H_out, double* g0_out,
+                                   uint32_t* st, cudaStream_t s) {
+  const Layout L = layout(p, n_cand, TROT_FWD);
+  unsigned char* sb = static_cast<unsigned char*>(scratch);
+  CandCoef* coef = reinterpret_cast<CandCoef*>(sb + L.coef);
+  float2* ek = reinterpret_cast<float2*>(sb + L.ek);
+  double* gsc = reinterpret_cast<double*>(sb + L.gscale);
+  double* partial = reinterpret_cast<double*>(sb + L.partial);
+  unsigned* qctr = reinterpret_cast<unsigned*>(sb + L.queue);
+  cudaError_t e;
+  stage_begin(p, EER4D_STAGE_TROTTER, s);
+  k_prep<<<n_cand, 256, 0, s>>>(aberr, n_cand, p->d_pix, p->P_pad, p->P, p->g.dalpha_rad,
+                                p->g.lambda_A, coef, ek, st, 0, qctr);
+  k_gbar_part<<<1, 256, 0, s>>>(G, p->d_bfp, p->P_bf, (int)p->g.scan_ny, (double)p->F, g0_out, gsc);
+  count_launches(2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const TrotParams tp = trot_params(p, n_cand);
+  int nblk = 1;
+  e = n_cand == 1 ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial, nullptr,
+                                          qctr, &nblk, s)
+                  : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial,
+                                               nullptr, qctr, &nblk, s);
+  count_launches(1);
+  if (e != cudaSuccess) return e;
+  stage_end(p, EER4D_STAGE_TROTTER, s);
   return cudaSuccess;
+}
+
+cudaError_t launch_image_from_spectrum(const eer4d_plan* p, const float2* H_in, const double* g0,
+                                       int n_cand, void* scratch, float* phase_out, double* var_out,
+                                       cudaStream_t s) {
+  const Layout L = layout(p, n_cand, TROT_FWD);
+  unsigned char* sb = static_cast<unsigned char*>(scratch);
+  float2* H = reinterpret_cast<float2*>(sb + L.H);
+  double* vpart = reinterpret_cast<double*>(sb + L.vpart);
+  const size_t n = (size_t)n_cand * p->g.scan_ny * p->nkx;
+  k_scale_spectrum<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(H_in, g0, n, H);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return image_stage(p, H, n_cand, vpart, phase_out, var_out, s);
 }
 
 namespace {

@@ -27,12 +27,13 @@ class Reconstructor:
     int32[4] (zeroed at construction; see ``check``)."""
 
     def __init__(self, geom: dict, precision: int = L.FP32_FFT, norm: int = L.NORM_NONE,
-                 n_cand: int = 1, device=None, alloc_counts: bool = True):
+                 n_cand: int = 1, device=None, alloc_counts: bool = True,
+                 shard: tuple[int, int] | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("Reconstructor needs a CUDA GPU; there is no CPU path")
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
-            self.plan = L.Plan(geom, precision, norm)
+            self.plan = L.Plan(geom, precision, norm, shard=shard)
             cb, gb, sb = self.plan.workspace_bytes(n_cand)
             self.n_cand = n_cand
             self.work = torch.empty(cb, dtype=torch.uint8, device=self.device) if alloc_counts else None
@@ -107,6 +108,28 @@ class Reconstructor:
         ph = torch.empty(n, self.Ny, self.Nx, dtype=torch.float32, device=self.device) if phase else None
         var = torch.empty(n, dtype=torch.float64, device=self.device)
         L.ssb_reconstruct(self.plan, self.G, ab, self.scratch, ph, var, status=self.status)
+        return ph, var
+
+    def spectrum_partial(self, aberr: torch.Tensor):
+        """This plan's share of the spectrum for candidates [n][5]: H complex64
+        [n][Ny][Nx/2+1] and g0 float64 [2] (summable over pixel shards)."""
+        ab = aberr.to(self.device, torch.float64).reshape(-1, 5).contiguous()
+        n = ab.shape[0]
+        if n > self.n_cand:
+            raise ValueError(f"{n} candidates but workspace sized for {self.n_cand}")
+        H = torch.empty(n, self.Ny, self.info["nkx"], dtype=torch.complex64, device=self.device)
+        g0 = torch.empty(2, dtype=torch.float64, device=self.device)
+        L.ssb_spectrum_partial(self.plan, self.G, ab, self.scratch, H, g0, status=self.status)
+        return H, g0
+
+    def image_from_spectrum(self, H: torch.Tensor, g0: torch.Tensor, phase: bool = True):
+        """Phase images and variances from shares summed over every shard."""
+        n = H.shape[0]
+        if n > self.n_cand:
+            raise ValueError(f"{n} candidates but workspace sized for {self.n_cand}")
+        ph = torch.empty(n, self.Ny, self.Nx, dtype=torch.float32, device=self.device) if phase else None
+        var = torch.empty(n, dtype=torch.float64, device=self.device)
+        L.ssb_image_from_spectrum(self.plan, H.contiguous(), g0.contiguous(), n, self.scratch, ph, var)
         return ph, var
 
     def grad(self, aberr: torch.Tensor, grad_phase: torch.Tensor):

@@ -9,7 +9,9 @@ aberrations change) driven by the hand-written adjoint.
   update is host-side glue; the objective and gradient run in the kernels.
 * ``RefocusGraph``: the device-resident refocus step (``ssb_refocus_step``:
   V, gradient, phase image and a fixed-step ascent update of the aberrations in
-  device memory) captured once as a CUDA graph and replayed.
+  device memory; or ``ssb_refocus_step_adam`` with an Adam update whose
+  moments also live in device memory) captured once as a CUDA graph and
+  replayed.
 """
 
 from __future__ import annotations
@@ -62,13 +64,22 @@ def fit(rec: Reconstructor, theta0, steps: int = 30, lr: float = 0.05,
 class RefocusGraph:
     """A captured CUDA graph of one ``ssb_refocus_step``: the aberrations,
     step sizes and outputs live in device memory, so every replay continues
-    from the previous one's update."""
+    from the previous one's update.  With ``adam`` (a learning rate per
+    parameter in units of ``scales``; 0 holds a parameter) each replay is an
+    Adam step instead of a fixed one; ``reset`` restarts it."""
 
-    def __init__(self, rec: Reconstructor, theta0, step, warmup: int = 2):
+    def __init__(self, rec: Reconstructor, theta0, step=None, warmup: int = 2, adam=None,
+                 scales=SCALES):
         dev = rec.device
         self.rec = rec
         self.theta = torch.as_tensor(theta0, dtype=torch.float64).to(dev).contiguous().clone()
-        self.step = torch.as_tensor(step, dtype=torch.float64).to(dev).contiguous().clone()
+        self.adam = adam is not None
+        if self.adam:
+            self.step = torch.tensor(list(adam) + list(scales), dtype=torch.float64, device=dev)
+        else:
+            self.step = torch.as_tensor(step, dtype=torch.float64).to(dev).contiguous().clone()
+        self.state = torch.zeros(11, dtype=torch.float64, device=dev)
+        self.theta0 = self.theta.clone()
         self.var = torch.empty(1, dtype=torch.float64, device=dev)
         self.grad = torch.empty(5, dtype=torch.float64, device=dev)
         self.phase = torch.empty(rec.Ny, rec.Nx, dtype=torch.float32, device=dev)
@@ -80,14 +91,26 @@ class RefocusGraph:
                 self._call()
         torch.cuda.current_stream().wait_stream(s)
         self.theta.copy_(th_save)
+        self.state.zero_()
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             self._call()
 
     def _call(self):
-        L.ssb_refocus_step(self.rec.plan, self.rec.G, self.theta, self.step, self.rec.scratch,
-                           self.var, self.grad, self.phase, status=self.rec.status)
+        if self.adam:
+            L.ssb_refocus_step_adam(self.rec.plan, self.rec.G, self.theta, self.step, self.state,
+                                    self.rec.scratch, self.var, self.grad, self.phase,
+                                    status=self.rec.status)
+        else:
+            L.ssb_refocus_step(self.rec.plan, self.rec.G, self.theta, self.step, self.rec.scratch,
+                               self.var, self.grad, self.phase, status=self.rec.status)
+
+    def reset(self, theta0=None):
+        """Back to ``theta0`` (default: the start) with fresh Adam moments."""
+        self.theta.copy_(self.theta0 if theta0 is None else
+                         torch.as_tensor(theta0, dtype=torch.float64).to(self.theta.device))
+        self.state.zero_()
 
     def replay(self, n: int = 1):
         for _ in range(n):

@@ -1,0 +1,181 @@
+"""GPU path against the FP64 oracle at the full sizes of the workloads.
+
+* The 1024x1024 workload the benchmark times (576x576 detector binned 6x, 553
+  bright-field pixels, about 5.2e7 events), through the benchmark's calls and
+  autotuned launch shapes: per-frame COM sums bit-exact over the whole scan,
+  COM maps and DPC within 1e-5, SSB phase within 1e-5 relative L2 and V within
+  1e-5 of the oracle's pixel-chunked SSB (Sec. IV Eq. 3; Sec. V Eq. 4).
+* The split-FP16 tensor-core DFT on the 256x256 precision workload (several
+  K tiles, so the stage ring wraps; two N tiles with a short last one, so the
+  second tensor-memory accumulator is used): SSB phase within 1e-4 relative
+  L2 of the oracle (the split form's tolerance), G within 1e-6 of max|G| of
+  the FP32 FFT.
+* The adjoint on the differentiation workload's optics (25 mrad, 1941
+  bright-field pixels, true C1 = 8 nm, C12 = 3 nm at 30 deg, C3 = 1 um) at a
+  256x256 scan: dV/dtheta per component within 1e-4 of the oracle.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SCALES = np.array([100.0, 50.0, 50.0, 1.0e4, 0.1])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2104_06336_gb300.buildlib import build
+    build()
+    import paper_2104_06336_gb300 as P
+    P.load()
+    return P
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_benchmarked_workload_step_matches_oracle():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(5)
+    geom = synth.geometry(w)
+    d = synth.generate(w, "cuda")
+    idx, off = d.idx.contiguous(), d.off.contiguous()
+    rec = P.Reconstructor(geom)
+    P.tuning.autotune(rec, idx, off)
+    F = w.n_frames
+    sums = torch.empty(3, F, dtype=torch.int64, device="cuda")
+    com = torch.empty(2, F, dtype=torch.float32, device="cuda")
+    dpc = torch.empty(w.scan_ny, w.scan_nx, dtype=torch.float32, device="cuda")
+    ph = torch.empty(1, w.scan_ny, w.scan_nx, dtype=torch.float32, device="cuda")
+    var = torch.empty(1, dtype=torch.float64, device="cuda")
+    ab = (40.0, 5.0, -5.0, 0.0, 0.0)
+    theta = torch.tensor(ab, dtype=torch.float64, device="cuda")
+    rec.totals.zero_()
+    P.ssb_accumulate_com(rec.plan, idx, off, 0, rec.work, rec.G, True, sums, rec.totals,
+                         status=rec.status)
+    P.com_dpc_sums(rec.plan, sums, com, dpc, totals=rec.totals, scratch=rec.scratch, status=rec.status)
+    P.ssb_reconstruct(rec.plan, rec.G, theta, rec.scratch, ph, var, status=rec.status)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    assert rec.info["P"] == 553
+    idx_np, off_np = d.numpy()
+    del d, idx, off
+    sx, sy, n = orc.com_sums(idx_np, off_np, w.det_w, w.det_h)
+    np.testing.assert_array_equal(sums.cpu().numpy(), np.stack([sx, sy, n]))
+    assert rec.totals.cpu().tolist() == [int(sx.sum()), int(sy.sum()), int(n.sum())]
+    ox, oy = orc.com_maps(sx, sy, n, *orc.pacbed_centre(sx, sy, n))
+    assert rel_l2(com.cpu().numpy(), np.stack([ox, oy])) <= 1e-6
+    e_dpc = rel_l2(dpc.cpu().numpy(), orc.idpc(ox, oy, geom))
+    phi, V = orc.ssb_phase_from_events(idx_np, off_np, geom, ab, "none")
+    e_ssb = rel_l2(ph[0].cpu().numpy(), phi)
+    print(f"1024^2 bench step: DPC rel L2 {e_dpc:.2e}, SSB rel L2 {e_ssb:.2e}, "
+          f"V rel {abs(float(var) - V) / V:.2e}")
+    assert e_dpc <= 1e-5
+    assert e_ssb <= 1e-5
+    assert abs(float(var) - V) <= 1e-5 * V
+
+
+@pytest.fixture(scope="module")
+def precision_case():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(2)
+    geom = synth.geometry(w)
+    d = synth.generate(w, "cuda")
+    idx_np, off_np = d.numpy()
+    G = orc.g_function(orc.densify(idx_np, off_np, geom), geom)
+    return w, geom, d, G
+
+
+@pytest.mark.parametrize("scan", [(256, 256), (96, 200)])
+def test_split_fp16_dft_at_size_matches_oracle(precision_case, scan):
+    """(96, 200): scan_nx/2 + 1 = 101 complex columns fill 202 of 256 rows of
+    one N tile (the short last tile alone) and K = 200 is not a multiple of
+    the 64-wide K tile."""
+    import paper_2104_06336_gb300 as P
+    if scan == (256, 256):
+        w, geom, d, G = precision_case
+    else:
+        w = synth.workload(2, scan_ny=scan[0], scan_nx=scan[1])
+        geom = synth.geometry(w)
+        d = synth.generate(w, "cuda")
+        i_np, o_np = d.numpy()
+        G = orc.g_function(orc.densify(i_np, o_np, geom), geom)
+    rs = P.Reconstructor(geom, precision=P.SPLIT_FP16)
+    rs.load(d.idx, d.off)
+    rf = P.Reconstructor(geom)
+    rf.load(d.idx, d.off)
+    torch.cuda.synchronize()
+    assert rs.check() == 0 and rf.check() == 0
+    Gs, Gf = rs.G_complex(), rf.G_complex()
+    eg = float((Gs - Gf).abs().max() / Gf.abs().max())
+    ab = (80.0, 15.0, 25.98, 1.0e4, 0.0)
+    ph, var = rs.reconstruct(torch.tensor(ab, dtype=torch.float64))
+    phi, V = orc.ssb_phase(G, geom, ab, "none")
+    e = rel_l2(ph[0].cpu().numpy(), phi)
+    print(f"split-FP16 {scan}: G vs FP32 {eg:.2e}, SSB rel L2 vs oracle {e:.2e}")
+    assert eg <= 1e-6
+    assert e <= 1e-4
+    assert abs(float(var) - V) <= 1e-4 * V
+
+
+def test_adjoint_on_differentiation_optics_at_256():
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(3, scan_ny=256, scan_nx=256)
+    geom = synth.geometry(w)
+    d = synth.generate(w, "cuda")
+    rec = P.Reconstructor(geom)
+    rec.load(d.idx, d.off)
+    torch.cuda.synchronize()
+    assert rec.info["P_bf"] == 1941
+    idx_np, off_np = d.numpy()
+    G = orc.g_function(orc.densify(idx_np, off_np, geom), geom)
+    for theta in (np.array(w.aberr), np.array([50.0, 10.0, -20.0, 2.0e3, 0.05])):
+        V, g, _ = rec.variance_grad(torch.tensor(theta))
+        Vr, gr, _ = orc.ssb_value_and_grad_var(G, geom, theta, "none")
+        assert abs(float(V) - Vr) <= 1e-5 * Vr
+        tol = 1e-4 * np.max(np.abs(gr) * SCALES) / SCALES
+        gg = g.cpu().numpy()
+        print("adjoint 256^2:", gg, gr)
+        assert np.all(np.abs(gg - gr) <= tol + 1e-4 * np.abs(gr)), (gg, gr)
+
+
+def test_refocus_fit_from_zero_on_differentiation_workload():
+    """The differentiation workload at full size (512x512 scan, 25 mrad,
+    40 e-/frame; true C1 = 8 nm, C12 = 3 nm at 30 deg, C3 = 1 um; Sec. IV /
+    Fig. 2 refocusing, driven by the adjoint instead of sliders): Adam ascent on
+    the image variance started from all aberrations zero, with no sweep seed
+    and no band limit, both as host-driven steps (refocus.fit) and as a
+    replayed CUDA graph of the device-side step (ssb_refocus_step_adam).
+    Tolerances (the variance maximum of a noisy dataset need not sit exactly
+    on the true values): C1 within 3 A, C12a and C12b within 1 A, C3 within
+    2500 A; V at the fit within 1e-3 of V at the true aberrations or above."""
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(3)
+    d = synth.generate(w, "cuda")
+    rec = P.Reconstructor(synth.geometry(w))
+    rec.load(d.idx, d.off)
+    true = np.array(w.aberr)
+    V_true = float(rec.variance_grad(torch.tensor(true))[0])
+    tol = np.array([3.0, 1.0, 1.0, 2500.0])
+    theta, hist = P.refocus.fit(rec, [0.0] * 5, steps=200, lr=0.05, mask=(1, 1, 1, 1, 0))
+    th = theta.cpu().numpy()
+    print("host-driven fit:", th, hist[0], hist[-1], V_true)
+    assert np.all(np.abs(th[:4] - true[:4]) <= tol), th
+    assert hist[-1] >= V_true * (1 - 1e-3)
+    g = P.refocus.RefocusGraph(rec, [0.0] * 5, adam=[0.05, 0.05, 0.05, 0.05, 0.0])
+    g.replay(200)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    tg = g.theta.cpu().numpy()
+    Vg = float(rec.variance_grad(g.theta)[0])
+    print("graph-replayed fit:", tg, Vg)
+    assert np.all(np.abs(tg[:4] - true[:4]) <= tol), tg
+    assert Vg >= V_true * (1 - 1e-3)

@@ -483,6 +483,40 @@ def test_ssb_on_poisson_events_follows_shot_noise():
     assert abs(r300 - pred) <= 0.06, (r30, r300, pred)
 
 
+@pytest.mark.parametrize("norm", ["none", "area"])
+def test_ssb_from_events_by_pixel_chunks_equals_full_path(norm):
+    """The pixel-chunked path (densify a few bright-field pixels at a time,
+    transform, add their trotter terms) gives the phase of the full path
+    (densify all pixels, G of every pixel, one trotter sum), to rounding."""
+    w = synth.workload(2, scan_ny=16, scan_nx=24)
+    geom = synth.geometry(w)
+    idx, off = synth.generate(w).numpy()
+    ab = (60.0, 10.0, -20.0, 5.0e3, 0.2)
+    phi, V = orc.ssb_phase(orc.g_function(orc.densify(idx, off, geom), geom), geom, ab, norm)
+    phc, Vc = orc.ssb_phase_from_events(idx, off, geom, ab, norm, chunk=37)
+    assert np.abs(phc - phi).max() <= 1e-10 * np.abs(phi).max()
+    assert abs(Vc - V) <= 1e-10 * V
+
+
+def test_ssb_spectrum_is_a_sum_over_pixels():
+    """S(K) and |K(K)| over disjoint pixel subsets add up to the full ones
+    (Eq. 3 is a sum over k): the property a pixel-sharded reconstruction rests
+    on."""
+    w = synth.workload(1)
+    geom = synth.geometry(w)
+    idx, off = synth.generate(w).numpy()
+    G = orc.g_function(orc.densify(idx, off, geom), geom)
+    ab = (40.0, 5.0, -5.0, 0.0, 0.3)
+    S, nK = orc.ssb_spectrum(G, geom, ab)
+    P_ = G.shape[0]
+    a, b = np.arange(0, P_ // 3), np.arange(P_ // 3, P_)
+    Sa, na = orc.ssb_spectrum(G[a], geom, ab, pixels=a)
+    Sb, nb = orc.ssb_spectrum(G[b], geom, ab, pixels=b)
+    assert na.sum() > 0 and nb.sum() > 0
+    np.testing.assert_array_equal(na + nb, nK)
+    assert np.abs(Sa + Sb - S).max() <= 1e-10 * np.abs(S).max()
+
+
 def test_aberration_correction_sign():
     """Reading of Eq. 3 under numpy's sign: reconstructing with the true
     aberrations beats no correction and the conjugate correction."""
