@@ -381,6 +381,21 @@ def run_ours(args, rank, world, local_rank):
                 acc()
             b.record()
             torch.cuda.synchronize()
+            # per-stage times of one more call (stage events on the launching stream)
+            sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nst)]
+            for e0, e1 in sev:
+                e0.record()
+                e1.record()
+            torch.cuda.synchronize()
+            P.eer4d_set_stage_events(rf.plan, [e[0] for e in sev], [e[1] for e in sev])
+            m0 = torch.cuda.Event(enable_timing=True)
+            m0.record()
+            acc()
+            torch.cuda.synchronize()
+            P.eer4d_set_stage_events(rf.plan)
+            f_stages = {n: round(sev[i][0].elapsed_time(sev[i][1]), 4) for i, n in enumerate(P._lib.STAGES)
+                        if m0.elapsed_time(sev[i][0]) >= 0.0}
             ph_f = torch.empty(1, Ny, w.scan_nx, dtype=torch.float32, device=dev)
             P.ssb_reconstruct(rf.plan, rf.G, theta, rf.scratch, ph_f, v1, status=rf.status)
             torch.cuda.synchronize()
@@ -388,7 +403,8 @@ def run_ours(args, rank, world, local_rank):
             if name == "fp32_fused":
                 ref_ph.copy_(ph_f)
             err = float((ph_f - ref_ph).double().norm() / ref_ph.double().norm())
-            forms[name] = {"accumulate_ms": a.elapsed_time(b) / 3, "phase_rel_l2_vs_fused": err}
+            forms[name] = {"accumulate_ms": a.elapsed_time(b) / 3, "stages_ms": f_stages,
+                           "phase_rel_l2_vs_fused": err}
             del rf
             torch.cuda.empty_cache()
         out["dft_forms"] = forms

@@ -103,6 +103,8 @@ void free_plan(eer4d_plan* p) {
   cudaFree(p->d_tw_x2);
   cudaFree(p->d_dft_hi);
   cudaFree(p->d_dft_lo);
+  cudaFree(p->d_tc4_tabs);
+  cudaFree(p->d_tc4_tw);
   free(p);
 }
 
@@ -315,6 +317,11 @@ static int create_plan(const eer4d_geom* h_geom, int precision, int norm, int sh
     p->d_tl_qp = nullptr;
     p->d_tl_n = nullptr;
     p->d_tl_order = nullptr;
+  }
+  if (precision == EER4D_SPLIT_FP16 && g.scan_nx == 1024 && (e = make_dftx_tc4(p)) != cudaSuccess) {
+    const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);
+    free_plan(p);
+    return rc;
   }
   if (precision == EER4D_SPLIT_FP16 && (e = make_dftx_tc(p)) != cudaSuccess) {
     const int rc = e == cudaErrorMemoryAllocation ? EER4D_ENOMEM : cuda_fail(e);

@@ -81,6 +81,8 @@ struct eer4d_plan {
   int32_t* d_bfp;            // [P_bf] kept-pixel index of each bright-field pixel (row-major)
   __half* d_dft_hi;          // split-FP16 DFT matrix along x (tile-blocked), SPLIT_FP16 plans
   __half* d_dft_lo;
+  unsigned char* d_tc4_tabs;  // four-step tensor-core DFT: split factor matrices (SPLIT_FP16, 1024 columns)
+  float2* d_tc4_tw;           // and its twiddles W1024^(xl kl) / 2 [32][17]
   int4* d_rows;              // [n_rows] (ky, bf kx lo, bf kx hi, p at bf lo)
   uint32_t* d_tl_bits;       // trotter membership lists at rotation 0 (NULL: none)
   uint32_t* d_tl_qp;
@@ -178,6 +180,14 @@ cudaError_t launch_stage1(const eer4d_plan* p, const __half* counts, float2* G, 
                           cudaStream_t s);
 cudaError_t launch_stage2(const eer4d_plan* p, const float2* X1, float2* G, cudaStream_t s);
 cudaError_t make_dftx_tc(eer4d_plan* p);
+// exp(-2 pi i k x / n), component c (0 cos, 1 -sin), from the exact integer
+// phase index (k x) mod n, split as hi = fp16(w), lo = fp16(w - hi)
+void dft_split_factor(int n, long long k, long long x, int c, __half* hi, __half* lo);
+// four-step tensor-core DFT along x for 1024-column scans
+cudaError_t make_dftx_tc4(eer4d_plan* p);
+bool dftx_tc4_ok(const eer4d_plan* p);
+cudaError_t launch_stage1_tc4(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
+                              uint32_t* st, cudaStream_t s);
 cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
                              uint32_t* st, cudaStream_t s);
 cudaError_t launch_transpose(const float2* in, float2* out, int rows, int cols, int batch,

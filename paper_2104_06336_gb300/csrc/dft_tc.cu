@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -32,114 +33,6 @@ constexpr int kK = 64;        // K per stage (fp16: 128 bytes per row)
 constexpr int kThreadsTC = 256;
 constexpr int kTileA = kM * kK * 2;   // 16 KB
 constexpr int kTileB = kN * kK * 2;   // 32 KB
-constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;  // 200 ms
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (r, k) in a K-major no-swizzle tile with kK columns
-__device__ __forceinline__ uint32_t cm_off(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// shared-memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30),
-// SBO >> 4 [32,46), descriptor version 1 at bit 46, no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
-}
-
-// instruction descriptor, kind::f16: D f32 (bit 4), A/B f16, both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait: returns false if the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (gtimer() - t0 > kWaitNs) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(dst_smem)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// 16 consecutive 32-bit accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // counts: fp16 [P_pad][Ny*Nx]; Bhi/Blo: tile-blocked [NT][KT][kN x kK] in the
 // shared core-matrix layout; X1: complex64 [nkx][Ny][P_pad].  grid = (pixel
@@ -262,37 +155,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // drain accumulator b to X1 and arrive on acce[b].  Every wait is bounded.
 constexpr int kStages = 2;
 constexpr int kStageBytes = kTileA + 2 * kTileB;  // 80 KB, a multiple of 1024
-
-// K-major operand with 128-byte swizzle (rows of 64 fp16, 8-row atoms of
-// 1024 B): LBO unused (1), SBO 1024 B, layout type 2
-__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46) | (2ull << 61);
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_dftx_tc2(const __grid_constant__ CUtensorMap tmA, const unsigned char* __restrict__ Bhi,
@@ -425,7 +287,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // Host: one DFT factor exp(-2 pi i k x / n), component c (0 = cos, 1 = -sin),
 // from the exact integer phase index (k x) mod n in double, split as
 // hi = fp16(w), lo = fp16(w - hi).
-static void dft_split(int n, long long k, long long x, int c, __half* hi, __half* lo) {
+void dft_split_factor(int n, long long k, long long x, int c, __half* hi, __half* lo) {
   const double tp = 6.283185307179586476925286766559;
   const long long e = (k * x) % n;
   const double w = c ? -sin(tp * (double)e / n) : cos(tp * (double)e / n);
@@ -439,7 +301,7 @@ extern "C" int eer4d_dft_split_factors(int n, int n_k, uint16_t* h_hi, uint16_t*
     for (int x = 0; x < n; ++x)
       for (int c = 0; c < 2; ++c) {
         __half hi, lo;
-        dft_split(n, k, x, c, &hi, &lo);
+        dft_split_factor(n, k, x, c, &hi, &lo);
         const size_t o = ((size_t)k * n + x) * 2 + c;
         h_hi[o] = __half_as_ushort(hi);
         h_lo[o] = __half_as_ushort(lo);
@@ -462,7 +324,7 @@ cudaError_t make_dftx_tc(eer4d_plan* p) {
         for (int k = 0; k < kK; ++k) {
           const int n = nt * kN + r, x = kt * kK + k, kx = n >> 1;
           __half h = __float2half_rn(0.f), l = h;
-          if (x < Nx && kx < nkx) dft_split(Nx, kx, x, n & 1, &h, &l);
+          if (x < Nx && kx < nkx) dft_split_factor(Nx, kx, x, n & 1, &h, &l);
           const size_t o = ((size_t)(r >> 3) * 1024 + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2;
           th[o] = h;
           tl[o] = l;
@@ -477,29 +339,12 @@ cudaError_t make_dftx_tc(eer4d_plan* p) {
   return cudaMemcpy(p->d_dft_lo, lo.data(), lo.size() * sizeof(__half), cudaMemcpyHostToDevice);
 }
 
-namespace {
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_fn() {
-  static std::once_flag once;
-  static EncodeTiledFn fn = nullptr;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-  });
-  return fn;
-}
-}  // namespace
-
 cudaError_t launch_stage1_tc(const eer4d_plan* p, const __half* counts, float2* X1, int y0, int y1,
                              uint32_t* st, cudaStream_t s) {
   if (y1 <= y0) return cudaSuccess;
+  // 1024 columns: the four-step form (two DFT-32 contractions per row)
+  if (dftx_tc4_ok(p) && (reinterpret_cast<uintptr_t>(counts) & 15) == 0)
+    return launch_stage1_tc4(p, counts, X1, y0, y1, st, s);
   const int Nx = p->g.scan_nx, Ny = p->g.scan_ny;
   const int KT = (Nx + kK - 1) / kK;
   const int NT = (2 * p->nkx + kN - 1) / kN;

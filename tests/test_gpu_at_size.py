@@ -179,3 +179,34 @@ def test_refocus_fit_from_zero_on_differentiation_workload():
     print("graph-replayed fit:", tg, Vg)
     assert np.all(np.abs(tg[:4] - true[:4]) <= tol), tg
     assert Vg >= V_true * (1 - 1e-3)
+
+
+@pytest.mark.parametrize("cfg,scan", [(5, (16, 1024)), (2, (8, 1024))])
+def test_split_fp16_four_step_dft_1024_columns(cfg, scan):
+    """Scans of 1024 columns take the four-step tensor-core DFT along x (two
+    DFT-32 contractions per row on tcgen05, the second on the split fp16
+    intermediate): G within 1e-6 of max|G| of the FP32 FFT and the SSB phase
+    within 1e-4 relative L2 of the oracle (553 and 1245 bright-field pixels)."""
+    import paper_2104_06336_gb300 as P
+    w = synth.workload(cfg, scan_ny=scan[0], scan_nx=scan[1])
+    geom = synth.geometry(w)
+    d = synth.generate(w, "cuda")
+    rs = P.Reconstructor(geom, precision=P.SPLIT_FP16)
+    rs.load(d.idx, d.off)
+    rf = P.Reconstructor(geom, precision=P.FP32_FFT_2PASS)
+    rf.load(d.idx, d.off)
+    torch.cuda.synchronize()
+    assert rs.check() == 0 and rf.check() == 0
+    Gs, Gf = rs.G_complex(), rf.G_complex()
+    eg = float((Gs - Gf).abs().max() / Gf.abs().max())
+    idx_np, off_np = d.numpy()
+    G = orc.g_function(orc.densify(idx_np, off_np, geom), geom)
+    ab = (40.0, 5.0, -5.0, 0.0, 0.0)
+    ph, var = rs.reconstruct(torch.tensor(ab, dtype=torch.float64))
+    phi, V = orc.ssb_phase(G, geom, ab, "none")
+    e = rel_l2(ph[0].cpu().numpy(), phi)
+    Gh = np.transpose(Gs.cpu().numpy()[:, :rs.info["P"], :], (1, 2, 0)).astype(np.complex128)
+    eo = np.abs(Gh - G[:, :, :scan[1] // 2 + 1]).max() / np.abs(G).max()
+    print(f"four-step split-FP16 {scan}: G vs FP32 {eg:.2e}, G vs oracle {eo:.2e}, SSB vs oracle {e:.2e}")
+    assert eg <= 1e-6 and eo <= 1e-6
+    assert e <= 1e-4
