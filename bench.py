@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=5)
     ap.add_argument("--scan", type=int, default=0, help="smaller square scan of the same geometry (profiling)")
+    ap.add_argument("--scan-shape", default="", help="NYxNX scan of the same geometry (profiling), e.g. 256x1024")
     ap.add_argument("--crop-px", type=float, default=0.0,
                     help="crop radius in binned pixels (default: the bright-field disk); 48 on the "
                          "1024x1024 workload keeps the disk inscribed in the 96x96 pattern")
@@ -249,6 +250,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     over = dict(scan_ny=args.scan, scan_nx=args.scan) if args.scan else {}
+    if args.scan_shape:
+        ny, nx = (int(v) for v in args.scan_shape.lower().split("x"))
+        over = dict(scan_ny=ny, scan_nx=nx)
     w = synth.workload(args.workload, seed=synth.workload(args.workload).seed + 1000 * rank, **over)
     geom = synth.geometry(w)
     if args.crop_px:

@@ -49,6 +49,7 @@ extern "C" {
 #define EER4D_ENOMEM    -7  /* plan tables could not be allocated */
 #define EER4D_EORDER    -8  /* ssb_accumulate chunks not delivered in frame order */
 #define EER4D_ESCRATCH  -9  /* plan needs more than the static scratch of ssb_reconstruct_static */
+#define EER4D_EBOUNDS  -10  /* a bounds check of the EER4D_CHECKS debug build failed (device) */
 
 /* ---- device status bits (d_status[0]) ---------------------------------- */
 #define EER4D_ST_RANGE    0x01u
@@ -56,6 +57,8 @@ extern "C" {
 #define EER4D_ST_OVERFLOW 0x04u
 #define EER4D_ST_TIMEOUT  0x08u
 #define EER4D_ST_ROTATION 0x10u  /* candidates of one call differ in rotation */
+#define EER4D_ST_BOUNDS   0x20u  /* debug build (-DEER4D_CHECKS): an index derived from data or
+                                    tables fell outside its buffer; the access was skipped */
 
 /* ---- plan options ------------------------------------------------------- */
 #define EER4D_FP32_FFT   0  /* scan transform: FP32 radix FFT */

@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libeer4d.so")
 
 EER4D_OK, EER4D_EINVAL, EER4D_ERANGE, EER4D_EOFFSETS = 0, -1, -2, -3
 EER4D_EOVERFLOW, EER4D_ETIMEOUT, EER4D_ECUDA, EER4D_ENOMEM, EER4D_EORDER = -4, -5, -6, -7, -8
-EER4D_ESCRATCH = -9
+EER4D_ESCRATCH, EER4D_EBOUNDS = -9, -10
 STATIC_SCRATCH_BYTES = 8 << 20
 ST_RANGE, ST_OFFSETS, ST_OVERFLOW, ST_TIMEOUT, ST_ROTATION = 0x1, 0x2, 0x4, 0x8, 0x10
+ST_BOUNDS = 0x20
 FP32_FFT, SPLIT_FP16, FP32_FFT_2PASS, FP32_STOCKHAM = 0, 1, 2, 3
 NORM_NONE, NORM_AREA = 0, 1
 
@@ -96,11 +97,13 @@ class Eer4dError(RuntimeError):
 
 
 def load(path: str | None = None):
-    """Loads libeer4d.so (building it first is the caller's job: build.build())."""
+    """Loads libeer4d.so (building it first is the caller's job: build.build()).
+    The environment variable EER4D_LIBRARY names another build of the same
+    library (for example the bounds-checking debug build) to load instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("EER4D_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libeer4d.so not found at {path}; run paper_2104_06336_gb300.build.build()")
     lib = C.CDLL(path)

@@ -375,6 +375,7 @@ int eer4d_status_code(const uint32_t* st) {
   if (b & EER4D_ST_OVERFLOW) return EER4D_EOVERFLOW;
   if (b & EER4D_ST_TIMEOUT) return EER4D_ETIMEOUT;
   if (b & EER4D_ST_ROTATION) return EER4D_EINVAL;
+  if (b & EER4D_ST_BOUNDS) return EER4D_EBOUNDS;
   return EER4D_OK;
 }
 
@@ -390,6 +391,7 @@ const char* eer4d_strerror(int code) {
     case EER4D_ENOMEM: return "out of memory";
     case EER4D_EORDER: return "chunks not delivered in frame order";
     case EER4D_ESCRATCH: return "plan needs more scratch than the 8 MiB static array of ssb_reconstruct_static";
+    case EER4D_EBOUNDS: return "a bounds check of the debug build failed (access skipped)";
     default: return "unknown error";
   }
 }

@@ -124,6 +124,22 @@ __device__ __forceinline__ void st_add(uint32_t* st, int word, uint32_t n) {
   if (st && n) atomicAdd(st + word, n);
 }
 
+// ---------------------------------------------------------- bounds checks ---
+// Debug build (-DEER4D_CHECKS): EER4D_IN_RANGE(i, n, st) tests 0 <= i < n for
+// an index derived from data or tables before the access it guards; a
+// failure sets EER4D_ST_BOUNDS and the caller skips the access.  The release
+// build compiles the test to `true`.
+#ifdef EER4D_CHECKS
+__device__ __forceinline__ bool eer4d_in_range(long long i, long long n, uint32_t* st) {
+  if (i >= 0 && i < n) return true;
+  st_or(st, EER4D_ST_BOUNDS);
+  return false;
+}
+#define EER4D_IN_RANGE(i, n, st) eer4d_in_range((long long)(i), (long long)(n), (st))
+#else
+#define EER4D_IN_RANGE(i, n, st) true
+#endif
+
 // ------------------------------------------------------------ warp helpers ---
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

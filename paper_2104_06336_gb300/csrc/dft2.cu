@@ -224,6 +224,9 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     }
     __syncthreads();
     if (!s_ok) break;
+    // debug build: the decoded task lies inside the group, row and K_x ranges (CTA-uniform)
+    if (!EER4D_IN_RANGE(k.g, q.n_groups, st) || !EER4D_IN_RANGE(k.r, k.type ? q.n2 : q.n1, st))
+      continue;
     {
       // the next task is known: if it is a DFT along x, pull its counts rows
       // (GP rows of 2N bytes) from DRAM into L2 now, so its loads hit L2

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(kThreads4, 1)
     __syncthreads();
     // ---- staged rows out: X1[k][y][p0 .. p0 + 7], 16 bytes per thread -----
     float2* dst = X1 + (size_t)y * P_pad + (size_t)g * kPx;
-    for (int i = tid; i < kNk * (kPx / 2); i += kThreads4) {
+    const bool rows_ok = EER4D_IN_RANGE(y, Ny, st) && EER4D_IN_RANGE(g * kPx + kPx - 1, P_pad, st);
+    for (int i = tid; rows_ok && i < kNk * (kPx / 2); i += kThreads4) {
       const int k = i >> 2, q = i & 3;
       const float2 a = stg[k * kOutPitch + 2 * q], c = stg[k * kOutPitch + 2 * q + 1];
       *reinterpret_cast<float4*>(dst + (size_t)k * Ny * P_pad + 2 * q) = make_float4(a.x, a.y, c.x, c.y);

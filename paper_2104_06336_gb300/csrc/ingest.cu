@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
     if (tab_smem) {
       dw.divmod(v, y, x);
       const int u = tx[x], vv = ty[y];
-      return (u | vv) < 0 ? -1 : t2[vv * pw + u];
+      if ((u | vv) < 0 || !EER4D_IN_RANGE(vv * pw + u, pw * ph, st)) return -1;
+      return t2[vv * pw + u];
     }
     if (SUMS || !lutp) dw.divmod(v, y, x);
     if (lutp) return __ldg(lutp + v);
@@ -358,7 +359,8 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
             uint32_t ex = 0u, ey = 0u;
             const int pp = pixel(e, ex, ey) - p0;
             if constexpr (SUMS) { fsx[f] += ex; fsy[f] += ey; fsn[f] += 1u; }
-            if ((unsigned)pp < (unsigned)pc) atomicAdd(col + pp * TP, inc);
+            if ((unsigned)pp < (unsigned)pc && EER4D_IN_RANGE(pp * TP + (j >> 1), PC * TP, st))
+              atomicAdd(col + pp * TP, inc);
           }
         }
       }
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
             const uint32_t b = __reduce_add_sync(0xffffffffu, fsy[f]);
             const uint32_t c = __reduce_add_sync(0xffffffffu, fsn[f]);
             const int j = jg + f * nw;
-            if (lane == 0 && j < j1) {
+            if (lane == 0 && j < j1 && EER4D_IN_RANGE(tf0 + j, F, st)) {
               const uint64_t g = tf0 + j;  // frame of the dataset
               sums[g] = a;
               sums[F + g] = b;
@@ -405,6 +407,9 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
         h01 = __halves2half2(__ushort2half_rn((unsigned short)c0), __ushort2half_rn((unsigned short)c1));
         h23 = __halves2half2(__ushort2half_rn((unsigned short)c2), __ushort2half_rn((unsigned short)c3));
       }
+      if (!EER4D_IN_RANGE((long long)(p0 + p) * (long long)NR + (long long)(tf0 + 4 * w) + 3,
+                          (long long)P_pad * (long long)NR, st))
+        continue;
       __half* dst = counts + (size_t)(p0 + p) * NR + tf0 + 4 * w;
       if (full) {
         uint2 pk;

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kWarps * 32,
               const float2* __restrict__ W, float2* H, double* partial, int32_t* count,
               const uint32_t* __restrict__ tl_bits, const uint32_t* __restrict__ tl_qp,
               const int* __restrict__ tl_n, const int* __restrict__ tl_order, int tl_cap,
-              unsigned* qctr) {
+              unsigned* qctr, uint32_t* st) {
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
   extern __shared__ unsigned char smem_raw[];
   float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(kWarps * 32,
     const int* order = (dyn && lists) ? tl_order : nullptr;
     for (int u = dyn ? take() : gw; u < ntask; u = dyn ? take() : u + nwarps) {
       const int t = order ? __ldg(order + u) : u;
+      if (!EER4D_IN_RANGE(t, ntask, st)) continue;  // warp-uniform (t is the warp's task)
       const int mx = t / nyw;
       const int my = (t - mx * nyw) * 32 + lane;
       const bool active = my < P.Ny;
@@ -307,10 +308,17 @@ __global__ void __launch_bounds__(kWarps * 32,
         if (mAny == 0u) return;
         float2 gb[kBatch];
 #pragma unroll
-        for (int i = 0; i < kBatch; ++i)
-          gb[i] = ((mAny >> i) & 1u)
-                      ? Gl[(size_t)(PACKED ? (int)(xv[i] & 0xffffu) : sp[xv[i]]) * P.Ny]
-                      : make_float2(0.f, 0.f);
+        for (int i = 0; i < kBatch; ++i) {
+          float2 v = make_float2(0.f, 0.f);
+          if ((mAny >> i) & 1u) {
+            const int qi = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
+            if (EER4D_IN_RANGE(qi, P.P_bf, st)) {
+              const int prow = PACKED ? (int)(xv[i] & 0xffffu) : sp[qi];
+              if (EER4D_IN_RANGE(prow, P.P_pad, st)) v = Gl[(size_t)prow * P.Ny];
+            }
+          }
+          gb[i] = v;
+        }
         if (PACKED && !nyq_warp) {
           // every list entry has a member among the warp's lanes, and a lane
           // that is not a member of entry i holds G = 0 there, so its term is
@@ -318,7 +326,10 @@ __global__ void __launch_bounds__(kWarps * 32,
 #pragma unroll
           for (int i = 0; i < kBatch; ++i) {
             const bool memM = (mM >> i) & 1u;
-            const int q = (int)(xv[i] >> 16);
+            int q = (int)(xv[i] >> 16);
+#ifdef EER4D_CHECKS
+            if (q >= P.P_bf) q = 0;  // its G is 0 (checked above): the term is 0
+#endif
             const float2 g = gb[i];
             const float2 gg = memM ? make_float2(g.x, -g.y) : g;
             contrib(gg, memM ? Kmx : Kpx, memM ? Kmy : Kpy, skk[q], q, memM ? 0.f : 1.f, SP, SM, DP,
@@ -330,7 +341,10 @@ __global__ void __launch_bounds__(kWarps * 32,
         for (int i = 0; i < kBatch; ++i) {
           const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
           if (!(memP || memM)) continue;
-          const int q = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
+          int q = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
+#ifdef EER4D_CHECKS
+          if (q >= P.P_bf) q = 0;  // its G is 0 (checked above): the term is 0
+#endif
           const float2 kk = skk[q];
           const float2 g = gb[i];
           // Off Nyquist the two sets are disjoint, so one term per pixel: G into
@@ -350,7 +364,8 @@ __global__ void __launch_bounds__(kWarps * 32,
         // q (the same sums in the same order), 32 entries at a time: each
         // lane reads its own two membership words (bit i = entry e0 + i) and
         // one packed (q, p) entry, which the shuffles hand to every lane
-        const int n = tl_n[t];
+        int n = tl_n[t];
+        if (!EER4D_IN_RANGE(n, tl_cap + 1, st)) n = 0;
         const uint32_t* bits = tl_bits + (size_t)t * (tl_cap / 32) * 64;
         const uint32_t* qps = tl_qp + (size_t)t * tl_cap;
         for (int e0 = 0; e0 < n; e0 += 32) {
@@ -774,7 +789,7 @@ template <int MODE, int NC>
 cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
                      const CandCoef* coef, const float2* ek, const double* gsc, const float2* W,
                      float2* H, double* partial, int32_t* count, unsigned* qctr, int* nblk,
-                     cudaStream_t s) {
+                     cudaStream_t s, uint32_t* st) {
   const size_t sm = sizeof(float2) * p->P_bf + sizeof(int) * ((p->P_bf + 1) & ~1) +
                     sizeof(float2) * (size_t)NC * p->P_bf;
   const void* kern = (const void*)k_trotter<MODE, NC>;
@@ -783,7 +798,7 @@ cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
   *nblk = trot_blocks(p, kern, sm);
   k_trotter<MODE, NC><<<*nblk, kWarps * 32, sm, s>>>(tp, G, p->d_bfp, p->d_pix, coef, ek, gsc, W,
                                                      H, partial, count, p->d_tl_bits, p->d_tl_qp,
-                                                     p->d_tl_n, p->d_tl_order, p->tl_cap, qctr);
+                                                     p->d_tl_n, p->d_tl_order, p->tl_cap, qctr, st);
   return cudaGetLastError();
 }
 
@@ -863,17 +878,17 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   switch (mode) {
     case TROT_FWD:
       e = n_cand == 1
-              ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s)
-              : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
+              ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st)
+              : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st);
       break;
     case TROT_GRAD:
-      e = launch_k<TROT_GRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
+      e = launch_k<TROT_GRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st);
       break;
     case TROT_VARGRAD:
-      e = launch_k<TROT_VARGRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
+      e = launch_k<TROT_VARGRAD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st);
       break;
     default:
-      e = launch_k<TROT_COUNT, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s);
+      e = launch_k<TROT_COUNT, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st);
       break;
   }
   count_launches(1);
@@ -908,9 +923,9 @@ cudaError_t launch_trotter_partial(const eer4d_plan* p, const float2* G, const d
   const TrotParams tp = trot_params(p, n_cand);
   int nblk = 1;
   e = n_cand == 1 ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial, nullptr,
-                                          qctr, &nblk, s)
+                                          qctr, &nblk, s, st)
                   : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial,
-                                               nullptr, qctr, &nblk, s);
+                                               nullptr, qctr, &nblk, s, st);
   count_launches(1);
   if (e != cudaSuccess) return e;
   stage_end(p, EER4D_STAGE_TROTTER, s);
