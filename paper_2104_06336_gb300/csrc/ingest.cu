@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(kComThreads) k_com_from_sums(const long long* 
 // atomics; every (p, f) of the chunk is written exactly once, zeros included.
 // Events are read straight from global memory, a warp per four frames with its
 // lanes on consecutive events (128-byte loads, eight in flight per lane).
+// The frame offsets of a CTA's next tile are loaded one tile ahead (threads
+// below TF keep them in registers), so their latency overlaps a whole tile.
 // The pixel of an event comes from the binning tables x -> u, y -> v and
 // (v, u) -> kept pixel, copied once per CTA into shared memory (one divide
 // by det_w and three shared loads, no L2 round trip per event); detectors
@@ -290,6 +292,26 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
   const uint64_t end = first + nfr;
   const int QW = TW / 2;  // 8-byte groups per pixel row (a power of two)
   const int qs = __ffs(QW) - 1;
+  // threads < TF: raw offsets off[f], off[f+1] of their frame of the next
+  // tile, loaded one tile ahead so the load latency overlaps a whole tile
+  uint64_t na = 0, nb = 0;
+  auto tile_frames = [&](uint32_t tt, uint64_t& tf0_, int& j0_, int& j1_) {
+    uint32_t ft_, ch_;
+    nch.divmod(tt, ft_, ch_);
+    tf0_ = T0 + (uint64_t)ft_ * TF;
+    j0_ = tf0_ < first ? (int)(first - tf0_) : 0;
+    j1_ = tf0_ + TF > end ? (int)(end - tf0_) : TF;
+  };
+  if (threadIdx.x < TF && blockIdx.x < ntiles) {
+    uint64_t tf0_;
+    int j0_, j1_;
+    tile_frames(blockIdx.x, tf0_, j0_, j1_);
+    if ((int)threadIdx.x >= j0_ && (int)threadIdx.x < j1_) {
+      const uint64_t f = tf0_ + threadIdx.x - first;
+      na = off[f];
+      nb = off[f + 1];
+    }
+  }
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // tile t: frames of frame tile t / NCH, pixels of chunk t % NCH (the
     // chunks of one frame tile are neighbours in t, so its events are read
@@ -314,13 +336,31 @@ __global__ void __launch_bounds__(kThreads, SUMS ? 3 : EER4D_SCATTER_MINB) k_sca
       uint64_t lo = 0, hi = 0;
       bool b = false;
       if (threadIdx.x >= j0 && threadIdx.x < j1) {
-        frame_range(off, tf0 + threadIdx.x - first, n_idx, lo, hi, b);
+        // frame_range on the offsets loaded a tile ahead
+        const uint64_t a = na, bb = nb;
+        lo = a < n_idx ? a : n_idx;
+        const uint64_t tt2 = bb > lo ? bb : lo;
+        hi = tt2 < n_idx ? tt2 : n_idx;
+        b = (bb < a) || (bb > n_idx) || (a > n_idx);
         if (hi - lo > kMaxFrameEvents) { b = true; hi = lo + kMaxFrameEvents; st_or(st, EER4D_ST_OVERFLOW); }
         if (b) st_or(st, EER4D_ST_OFFSETS);
       }
       s_lo[threadIdx.x] = lo;
       s_n[threadIdx.x] = (uint32_t)(hi - lo);
       if (hi > lo) atomicMax(&s_maxev, (uint32_t)(hi - lo));
+      // the next tile's offsets, consumed one tile later
+      const uint32_t tn = t + gridDim.x;
+      na = nb = 0;
+      if (tn < ntiles) {
+        uint64_t tf0_;
+        int j0_, j1_;
+        tile_frames(tn, tf0_, j0_, j1_);
+        if ((int)threadIdx.x >= j0_ && (int)threadIdx.x < j1_) {
+          const uint64_t f = tf0_ + threadIdx.x - first;
+          na = off[f];
+          nb = off[f + 1];
+        }
+      }
     }
     __syncthreads();
     // a warp takes four frames at a time (j, j + nw, j + 2 nw, j + 3 nw) and
