@@ -513,6 +513,15 @@ def run_ours(args, rank, world, local_rank):
         fp32_peak = nsm * 128 * mhz * 1e6        # FP32 lanes per SM per clock
         mufu_peak = nsm * 16 * mhz * 1e6         # MUFU lanes per SM per clock
         t_alu = max(terms * 26 / fp32_peak, terms * 2 / mufu_peak)
+        # the adjoint step (V and five derivatives per term, FP64 block sums):
+        # about 26 forward and 65 derivative FP32-pipe operations per term
+        # (the five dpsi/dtheta and their two weighted accumulations each)
+        t_adj = lat[len(lat) // 2] * 1e-3
+        out["refocus"]["adjoint_step_roofline"] = {
+            "bound": "alu", "terms": float(sigma_k), "fp32_ops_per_term": 91,
+            "frac": float(sigma_k) * 91 / fp32_peak / t_adj,
+            "hbm_frac": (8 * sigma_k + 8 * Ny * nkx) / t_adj / 1e9 / hbm,
+        }
         out["refocus"]["batched_sweep64_roofline"] = {
             "bound": "alu", "terms": terms, "fp32_ops_per_term": 26, "mufu_ops_per_term": 2,
             "peak_fp32_ops_s": fp32_peak, "peak_mufu_ops_s": mufu_peak,
