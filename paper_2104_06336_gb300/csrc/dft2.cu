@@ -207,9 +207,11 @@ __global__ void __launch_bounds__(R1 * CP, EER4D_DFT2_MINB * 128 / (R1 * CP))
     const Task k = s_k[it % 3];
     if (k.type < 0) break;
     if (threadIdx.x == 0) {
+      // the publish fence first: it then waits only for the previous task's
+      // writes, not for the queue atomic issued below
+      if (pd.n && (pd.type != k.type || pd.g != k.g)) publish(pd, done1, done2);
       if (it > 0) s_k[(it + 1) % 3] = decode(inflight, q);
       inflight = atomicAdd(next, 1u);
-      if (pd.n && (pd.type != k.type || pd.g != k.g)) publish(pd, done1, done2);
       bool ok = true;
       if (k.type == 1 && k.g > known1) {
         publish(pd, done1, done2);
