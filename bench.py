@@ -411,6 +411,38 @@ def run_ours(args, rank, world, local_rank):
                            "phase_rel_l2_vs_fused": err}
             del rf
             torch.cuda.empty_cache()
+        # vendor library beside the fused form, for comparison only (it is not
+        # part of the path): cuFFT's batched 2D R2C (torch.fft.rfft2) of the
+        # same counts as fp32 [P_pad][Ny][Nx] (the conversion is not timed),
+        # output [P_pad][Ny][Nx/2+1] left in its own layout
+        if Ny == w.scan_nx:
+            rf = P.Reconstructor(geom, precision=P.FP32_FFT, device=dev)
+            P.ssb_accumulate(rf.plan, idx, off, 0, rf.work, rf.G, True, status=rf.status)
+            cnt32 = rf.counts.view(P_pad, Ny, w.scan_nx).float()
+            Gc = torch.fft.rfft2(cnt32)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                Gc = torch.fft.rfft2(cnt32)
+            b.record()
+            torch.cuda.synchronize()
+            # the same transform: our G [K_x][p][K_y] against the library's on
+            # three pixels, every K
+            Gv = torch.view_as_complex(rf.G.view(-1, 2)).view(nkx, P_pad, Ny)
+            num = den = 0.0
+            for pp in (0, P_pad // 2, rec.info["P"] - 1):
+                ours = Gv[:, pp, :].to(torch.complex128)
+                lib = Gc[pp].transpose(0, 1).to(torch.complex128)
+                num += float((ours - lib).abs().pow(2).sum())
+                den += float(lib.abs().pow(2).sum())
+            forms["cufft_rfft2_fp32_reference"] = {
+                "transform_ms": a.elapsed_time(b) / 3,
+                "what": "vendor cuFFT batched 2D R2C of the fp32 counts (comparison only, not the path); "
+                        "compare with fp32_fused stages_ms.dft_xy, which also reads fp16 and writes G transposed",
+                "G_rel_l2_vs_fused_3_pixels": (num / den) ** 0.5 if den > 0 else None}
+            del rf, cnt32, Gc, Gv
+            torch.cuda.empty_cache()
         out["dft_forms"] = forms
 
     # ---- end to end through the public API with host buffers -------------
