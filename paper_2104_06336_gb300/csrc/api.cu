@@ -752,10 +752,10 @@ int eer4d_autotune(eer4d_plan* p, const uint32_t* d_idx, uint64_t n_idx, const u
     rc = cuda_fail(launch_stage1(p, counts, X1, 0, (int)p->g.scan_ny, s));
     if (rc == EER4D_OK) rc = cuda_fail(launch_stage2(p, X1, G, s));
   }
-  // trotter: 1..4 CTAs per SM, one candidate
+  // trotter: 1..3 CTAs per SM, one candidate
   if (rc == EER4D_OK) {
     float tbest = -1.f;
-    for (int cps = 1; cps <= 4; ++cps) {
+    for (int cps = 1; cps <= 3; ++cps) {
       p->tune = best;
       p->tune.trotter_ctas_per_sm = cps;
       const float ms = time_ms(s, 2, [&] {

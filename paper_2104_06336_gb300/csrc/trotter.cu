@@ -33,13 +33,7 @@ namespace {
 
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr int kWarps = EER4D_WARPS_TROTTER;
-constexpr int kBatch = 8;  // pixels per batch of the trotter pixel loop (gradient modes, batched kernel)
-// The forward and count modes take batches of 4 at 4 CTAs per SM (64
-// registers): more warps in flight hide the G loads better than longer
-// batches (0.257 against 0.260 ms at 1024^2, identical sums: each lane adds
-// its terms in list order whatever the batch length).
-template <int MODE>
-constexpr int batch_len() { return (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 8 : 4; }
+constexpr int kBatch = 8;  // pixels per batch of the trotter pixel loop
 
 struct CandCoef {
   float a1, a2, a3, a4;  // chi/(2 pi) = a1 r2 + a2 (qx^2-qy^2) + a3 qx qy + a4 r2^2
@@ -177,7 +171,7 @@ __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, in
 // (|K(K)| per bin).
 template <int MODE, int NC>
 __global__ void __launch_bounds__(kWarps * 32,
-                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 4)
+                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 3)
     k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
               const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
@@ -186,7 +180,6 @@ __global__ void __launch_bounds__(kWarps * 32,
               const int* __restrict__ tl_n, const int* __restrict__ tl_order, int tl_cap,
               unsigned* qctr, uint32_t* st) {
   constexpr bool GRAD = (MODE == TROT_GRAD || MODE == TROT_VARGRAD);
-  constexpr int KB = batch_len<MODE>();
   extern __shared__ unsigned char smem_raw[];
   float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
   int* sp = reinterpret_cast<int*>(skk + P.P_bf);                      // [P_bf] kept-pixel index
@@ -302,21 +295,20 @@ __global__ void __launch_bounds__(kWarps * 32,
         }
       };
 
-      // A batch of KB bright-field pixels with this lane's membership bits:
-      // every member's G load is issued before any is used (KB loads in
+      // A batch of kBatch bright-field pixels with this lane's membership bits:
+      // every member's G load is issued before any is used (kBatch loads in
       // flight).  Entry xv[i] is q << 16 | p (bright-field index, kept pixel)
       // from the lists (PACKED), or the index q itself.
-      auto batch = [&](unsigned mP, unsigned mM, const uint32_t (&xv)[batch_len<MODE>()],
-                       auto packed) {
+      auto batch = [&](unsigned mP, unsigned mM, const uint32_t (&xv)[kBatch], auto packed) {
         constexpr bool PACKED = decltype(packed)::value;
         nP += __popc(mP);
         nM += __popc(mM);
         if (MODE == TROT_COUNT) return;
         const unsigned mAny = mP | mM;
         if (mAny == 0u) return;
-        float2 gb[KB];
+        float2 gb[kBatch];
 #pragma unroll
-        for (int i = 0; i < KB; ++i) {
+        for (int i = 0; i < kBatch; ++i) {
           float2 v = make_float2(0.f, 0.f);
           if ((mAny >> i) & 1u) {
             const int qi = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
@@ -332,7 +324,7 @@ __global__ void __launch_bounds__(kWarps * 32,
           // that is not a member of entry i holds G = 0 there, so its term is
           // exactly 0: the entries run as independent straight-line chains
 #pragma unroll
-          for (int i = 0; i < KB; ++i) {
+          for (int i = 0; i < kBatch; ++i) {
             const bool memM = (mM >> i) & 1u;
             int q = (int)(xv[i] >> 16);
 #ifdef EER4D_CHECKS
@@ -346,7 +338,7 @@ __global__ void __launch_bounds__(kWarps * 32,
           return;
         }
 #pragma unroll
-        for (int i = 0; i < KB; ++i) {
+        for (int i = 0; i < kBatch; ++i) {
           const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
           if (!(memP || memM)) continue;
           int q = PACKED ? (int)(xv[i] >> 16) : (int)xv[i];
@@ -381,20 +373,19 @@ __global__ void __launch_bounds__(kWarps * 32,
           const uint32_t wM = __ldg(bits + 2 * e0 + 32 + lane);
           const uint32_t ql = __ldg(qps + e0 + lane);  // tl_cap is a multiple of 32
           const int m = n - e0 < 32 ? n - e0 : 32;
-          for (int s0 = 0; s0 < m; s0 += KB) {
-            uint32_t xv[KB];
+          for (int s0 = 0; s0 < m; s0 += kBatch) {
+            uint32_t xv[kBatch];
 #pragma unroll
-            for (int i = 0; i < KB; ++i) xv[i] = __shfl_sync(0xffffffffu, ql, s0 + i);
-            batch((wP >> s0) & ((1u << KB) - 1u), (wM >> s0) & ((1u << KB) - 1u), xv,
-                  std::true_type{});
+            for (int i = 0; i < kBatch; ++i) xv[i] = __shfl_sync(0xffffffffu, ql, s0 + i);
+            batch((wP >> s0) & 0xffu, (wM >> s0) & 0xffu, xv, std::true_type{});
           }
         }
       } else {
-        for (int q0 = 0; q0 < P.P_bf; q0 += KB) {
+        for (int q0 = 0; q0 < P.P_bf; q0 += kBatch) {
           unsigned mP = 0u, mM = 0u;
-          uint32_t xv[KB];
+          uint32_t xv[kBatch];
 #pragma unroll
-          for (int i = 0; i < KB; ++i) {
+          for (int i = 0; i < kBatch; ++i) {
             const int q = q0 + i;
             xv[i] = q < P.P_bf ? q : 0;
             if (q >= P.P_bf) continue;
