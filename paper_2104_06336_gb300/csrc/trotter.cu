@@ -169,9 +169,12 @@ __device__ __forceinline__ float2 combine(float2 A, float2 B, int na, int nb, in
 // MODE: TROT_FWD (H for NC candidates per pass), TROT_GRAD (adjoint against
 // W = FFT(upstream gradient)), TROT_VARGRAD (V and dV/dtheta), TROT_COUNT
 // (|K(K)| per bin).
+// Register budgets: one candidate at 3 CTAs per SM (80 registers); several
+// candidates per pass (NC phase chains per term) and the gradient modes at 2,
+// so that their per-candidate sums stay in registers instead of spilling.
 template <int MODE, int NC>
 __global__ void __launch_bounds__(kWarps * 32,
-                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD) ? 2 : 3)
+                                  (MODE == TROT_GRAD || MODE == TROT_VARGRAD || NC > 1) ? 2 : 3)
     k_trotter(TrotParams P, const float2* __restrict__ G, const int32_t* __restrict__ bfp,
               const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
               const float2* __restrict__ ek, const double* __restrict__ gscale,
@@ -745,7 +748,12 @@ __global__ void k_adam(double* theta, const double* rate, double* state, const d
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int kNcFwd = 4;  // candidates per pass of the forward kernel
+// candidates per pass of the forward kernel: 8 when their phase tables
+// (8 x P_bf float2 in shared memory) still leave 2 CTAs per SM, else 4
+// (64 candidates at 1024^2: 12.9 ms with 8, 15.0 ms with 4; on the 512^2
+// 25 mrad optics, P_bf = 1963: 18.2 ms with 4, 24.2 ms with 8)
+constexpr int kNcFwd = 4;
+constexpr int kNcFwdWide = 8;
 
 constexpr int kMaxTrotBlocks = 2048;  // capacity of the per-block partial sums
 
@@ -785,13 +793,30 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   return L;
 }
 
+template <int NC>
+size_t trot_smem(const eer4d_plan* p) {
+  return sizeof(float2) * p->P_bf + sizeof(int) * ((p->P_bf + 1) & ~1) +
+         sizeof(float2) * (size_t)NC * p->P_bf;
+}
+
+// True when the forward kernel with kNcFwdWide candidates per pass keeps 2
+// resident CTAs per SM (its shared-memory tables grow with the candidates).
+bool fwd_wide_fits(const eer4d_plan* p) {
+  const void* kern = (const void*)k_trotter<TROT_FWD, kNcFwdWide>;
+  const size_t sm = trot_smem<kNcFwdWide>(p);
+  if (ensure_smem(kern, sm) != cudaSuccess) return false;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, sm) != cudaSuccess)
+    return false;
+  return occ >= 2;
+}
+
 template <int MODE, int NC>
 cudaError_t launch_k(const eer4d_plan* p, const TrotParams& tp, const float2* G,
                      const CandCoef* coef, const float2* ek, const double* gsc, const float2* W,
                      float2* H, double* partial, int32_t* count, unsigned* qctr, int* nblk,
                      cudaStream_t s, uint32_t* st) {
-  const size_t sm = sizeof(float2) * p->P_bf + sizeof(int) * ((p->P_bf + 1) & ~1) +
-                    sizeof(float2) * (size_t)NC * p->P_bf;
+  const size_t sm = trot_smem<NC>(p);
   const void* kern = (const void*)k_trotter<MODE, NC>;
   cudaError_t e = ensure_smem(kern, sm);
   if (e != cudaSuccess) return e;
@@ -879,6 +904,9 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
     case TROT_FWD:
       e = n_cand == 1
               ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st)
+          : fwd_wide_fits(p)
+              ? launch_k<TROT_FWD, kNcFwdWide>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr,
+                                               &nblk, s, st)
               : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, W, H, partial, count_out, qctr, &nblk, s, st);
       break;
     case TROT_GRAD:
@@ -922,10 +950,12 @@ cudaError_t launch_trotter_partial(const eer4d_plan* p, const float2* G, const d
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const TrotParams tp = trot_params(p, n_cand);
   int nblk = 1;
-  e = n_cand == 1 ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial, nullptr,
-                                          qctr, &nblk, s, st)
-                  : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial,
-                                               nullptr, qctr, &nblk, s, st);
+  e = n_cand == 1   ? launch_k<TROT_FWD, 1>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial, nullptr,
+                                            qctr, &nblk, s, st)
+      : fwd_wide_fits(p) ? launch_k<TROT_FWD, kNcFwdWide>(p, tp, G, coef, ek, gsc, nullptr, H_out,
+                                                         partial, nullptr, qctr, &nblk, s, st)
+                         : launch_k<TROT_FWD, kNcFwd>(p, tp, G, coef, ek, gsc, nullptr, H_out, partial,
+                                                      nullptr, qctr, &nblk, s, st);
   count_launches(1);
   if (e != cudaSuccess) return e;
   stage_end(p, EER4D_STAGE_TROTTER, s);
