@@ -177,6 +177,34 @@ def test_ssb_phase_fp32(which, ab, request):
     assert c.rec.check() == 0
 
 
+@pytest.mark.parametrize("which", ["c1", "c2small"])
+def test_many_candidates_several_passes_match_single(which, request):
+    """20 candidates: several passes of the multi-candidate kernel (8 or 4
+    per pass, chosen by the shared memory their phase tables need), spread
+    over a second grid dimension on these small scans.  Every candidate's
+    phase equals the one-candidate path bit for bit and its variance matches
+    the oracle's (Eq. 3)."""
+    import paper_2104_06336_gb300 as P
+    c = request.getfixturevalue(which)
+    rng = np.random.default_rng(7)
+    cands = np.zeros((20, 5))
+    cands[:, 0] = np.linspace(-150.0, 150.0, 20)
+    cands[:, 1] = rng.uniform(-20.0, 20.0, 20)
+    cands[:, 2] = rng.uniform(-20.0, 20.0, 20)
+    cands[:, 3] = rng.choice([0.0, 5.0e3], 20)
+    cands = torch.tensor(cands)
+    rec = P.Reconstructor(c.geom, n_cand=20)
+    rec.load(c.idx, c.off)
+    ph, var = rec.reconstruct(cands)
+    torch.cuda.synchronize()
+    assert rec.check() == 0
+    for i in (0, 7, 8, 13, 19):
+        p1, v1 = c.rec.reconstruct(cands[i])
+        assert torch.equal(ph[i], p1[0]), i
+        _, V = orc.ssb_phase(c.G_orc, c.geom, cands[i].numpy(), "none")
+        assert abs(float(var[i]) - V) <= 1e-5 * V, (i, float(var[i]), V)
+
+
 def test_batched_candidates_match_single(c1):
     import paper_2104_06336_gb300 as P
     cands = torch.tensor([[80.0, 15.0, 26.0, 1.0e4, 0.1], [0, 0, 0, 0, 0.1], [-200.0, -50.0, 30.0, 0, 0.1],
