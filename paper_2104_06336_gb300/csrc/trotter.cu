@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(kWarps * 32,
   float2* skk = reinterpret_cast<float2*>(smem_raw);                  // [P_bf] (kx, ky)
   int* sp = reinterpret_cast<int*>(skk + P.P_bf);                      // [P_bf] kept-pixel index
   float2* sek = reinterpret_cast<float2*>(sp + ((P.P_bf + 1) & ~1));  // [NC][P_bf]
-  __shared__ double sred[GRAD ? kWarps * 32 : 1][5];
 
   for (int q = threadIdx.x; q < P.P_bf; q += blockDim.x) {
     const int p = bfp[q];
@@ -204,7 +203,6 @@ __global__ void __launch_bounds__(kWarps * 32,
   const int ntask = P.nkx * nyw;
   const int gw = blockIdx.x * kWarps + warp;
   const int nwarps = gridDim.x * kWarps;
-  double gacc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const int npass = (MODE == TROT_FWD) ? (P.n_cand + NC - 1) / NC : 1;
 
   // passes of NC candidates; SPREAD: blockIdx.y takes passes y, y + gridDim.y,
@@ -227,9 +225,10 @@ __global__ void __launch_bounds__(kWarps * 32,
     for (int c = 0; c < NC; ++c) cf[c] = coef[cb + (c < ncp ? c : 0)];
 
     // Warp tasks come from a work queue (with the lists, longest first) when
-    // there is one pass and no gradient sums (whose order would then vary
-    // between runs); otherwise warp gw takes tasks gw, gw + nwarps, ...
-    const bool dyn = !GRAD && npass == 1 && qctr != nullptr;
+    // there is one pass; otherwise warp gw takes tasks gw, gw + nwarps, ...
+    // The gradient sums do not depend on the schedule: each task's share is
+    // summed over its warp in a fixed order and stored at the task's index.
+    const bool dyn = npass == 1 && qctr != nullptr;
     auto take = [&]() -> int {
       unsigned v = 0u;
       if (lane == 0) v = atomicAdd(qctr, 1u);
@@ -405,19 +404,15 @@ __global__ void __launch_bounds__(kWarps * 32,
         }
       }
 
-      if (!active) continue;
-      if (MODE == TROT_COUNT) {
-        count[my * P.Nx + mx] = nP;
-        count[mmy * P.Nx + mmx] = nM;
-        continue;
-      }
-      const float wgt = (mx == 0 || 2 * mx == P.Nx) ? 1.f : 2.f;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (c >= ncp) break;
-        const float2 Hb = combine(SP[c], SM[c], nP, nM, P.norm, scale);
-        if (MODE != TROT_GRAD) H[((size_t)(cb + c) * P.Ny + my) * P.nkx + mx] = Hb;
-        if constexpr (GRAD) {
+      if constexpr (GRAD) {
+        // this task's share of dV/dtheta, one bin per lane, stored at
+        // (task, lane): the sum over tasks and lanes runs afterwards in a
+        // fixed order, whatever warp took the task
+        double tv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (active) {
+          const float wgt = (mx == 0 || 2 * mx == P.Nx) ? 1.f : 2.f;
+          const float2 Hb = combine(SP[0], SM[0], nP, nM, P.norm, scale);
+          if (MODE != TROT_GRAD) H[(size_t)my * P.nkx + mx] = Hb;
           float2 wb;
           double f;
           if (MODE == TROT_VARGRAD) {  // dV/dtheta: w = 2 H / N_R, factor 1/N_R
@@ -430,21 +425,26 @@ __global__ void __launch_bounds__(kWarps * 32,
 #pragma unroll
           for (int j = 0; j < 5; ++j) {
             const float2 dH = combine(DP[j], DM[j], nP, nM, P.norm, scale);
-            gacc[j] += (double)wgt * f * ((double)dH.x * (double)wb.x + (double)dH.y * (double)wb.y);
+            tv[j] = (double)wgt * f * ((double)dH.x * (double)wb.x + (double)dH.y * (double)wb.y);
+          }
+        }
+        double* dst = partial + ((size_t)t * 32 + lane) * 5;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) dst[j] = tv[j];
+      } else {
+        if (!active) continue;
+        if constexpr (MODE == TROT_COUNT) {
+          count[my * P.Nx + mx] = nP;
+          count[mmy * P.Nx + mmx] = nM;
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (c >= ncp) break;
+            const float2 Hb = combine(SP[c], SM[c], nP, nM, P.norm, scale);
+            H[((size_t)(cb + c) * P.Ny + my) * P.nkx + mx] = Hb;
           }
         }
       }
-    }
-  }
-  if constexpr (GRAD) {
-    // fixed-order block sum of the per-thread partials (no warp intrinsics)
-#pragma unroll
-    for (int j = 0; j < 5; ++j) sred[threadIdx.x][j] = gacc[j];
-    __syncthreads();
-    if (threadIdx.x < 5) {
-      double s = 0.0;
-      for (int i = 0; i < kWarps * 32; ++i) s += sred[i][threadIdx.x];
-      partial[(size_t)blockIdx.x * 5 + threadIdx.x] = s;
     }
   }
 }
@@ -649,6 +649,28 @@ __global__ void k_reduce_partials(const double* partial, int nblk, int nv, doubl
   }
 }
 
+// First stage of a fixed-order sum of n rows of nv doubles: block b adds the
+// rows of its contiguous range [b*n/B, (b+1)*n/B), thread i every 256th from
+// the range start, then a fixed tree; out[b][j].
+constexpr int kRedBlocks = 152;
+__global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ in, long long n,
+                                                      int nv, double* out) {
+  __shared__ double red[256];
+  const long long b0 = n * blockIdx.x / gridDim.x, b1 = n * (blockIdx.x + 1) / gridDim.x;
+  for (int j = 0; j < nv; ++j) {
+    double s = 0.0;
+    for (long long r = b0 + threadIdx.x; r < b1; r += 256) s += in[r * nv + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)blockIdx.x * nv + j] = red[0];
+    __syncthreads();
+  }
+}
+
 // V_c = sum_b w(b) |H_c(b)|^2 / N_R^2 over the stored half: per-block partial
 // sums (grid kVarBlocks x n_cand), then a fixed-order final sum per candidate.
 constexpr int kVarBlocks = 128;
@@ -791,7 +813,14 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   L.gscale = o; o = align256(o + 2 * sizeof(double));
   const int nh = (mode == TROT_GRAD || mode == TROT_COUNT) ? 0 : n_cand;
   L.H = o; o = align256(o + sizeof(float2) * (size_t)nh * p->g.scan_ny * p->nkx);
-  L.partial = o; o = align256(o + sizeof(double) * 5 * kMaxTrotBlocks);
+  // per-block partial sums, or in the gradient modes one share per (warp
+  // task, lane) followed by the first-stage sums of the final reduction
+  size_t npart = kMaxTrotBlocks;
+  if (mode == TROT_GRAD || mode == TROT_VARGRAD) {
+    const size_t ntask = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
+    npart = ntask * 32 + kRedBlocks;
+  }
+  L.partial = o; o = align256(o + sizeof(double) * 5 * npart);
   L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)nh);
   L.queue = o; o = align256(o + sizeof(unsigned));
   L.total = o;
@@ -944,7 +973,13 @@ cudaError_t launch_trotter(const eer4d_plan* p, const float2* G, const double* a
   count_launches(1);
   if (e != cudaSuccess) return e;
   if (mode == TROT_GRAD || mode == TROT_VARGRAD) {
-    k_reduce_partials<<<1, 256, 0, s>>>(partial, nblk, 5, grad_out);
+    // the (task, lane) shares in a fixed order: contiguous ranges, then the
+    // range sums
+    const long long rows = (long long)p->nkx * (((int)p->g.scan_ny + 31) / 32) * 32;
+    double* stage = partial + rows * 5;
+    k_reduce_rows<<<kRedBlocks, 256, 0, s>>>(partial, rows, 5, stage);
+    k_reduce_partials<<<1, 256, 0, s>>>(stage, kRedBlocks, 5, grad_out);
+    count_launches(1);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
