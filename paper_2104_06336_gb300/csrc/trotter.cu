@@ -65,7 +65,7 @@ __global__ void k_prep(const double* __restrict__ aberr, int n_cand, const short
                        uint32_t* st, int own_rot = 0, unsigned* qctr = nullptr) {
   __shared__ CandCoef sc;
   const int c = blockIdx.x;
-  if (qctr && c == 0 && threadIdx.x == 0) *qctr = 0u;  // the trotter's work queue
+  if (qctr && threadIdx.x == 0) qctr[c] = 0u;  // the work queue of candidate pass c
   if (threadIdx.x == 0) {
     const double* a = aberr + 5 * c;
     const double d2 = dalpha * dalpha;
@@ -224,14 +224,15 @@ __global__ void __launch_bounds__(kWarps * 32,
 #pragma unroll
     for (int c = 0; c < NC; ++c) cf[c] = coef[cb + (c < ncp ? c : 0)];
 
-    // Warp tasks come from a work queue (with the lists, longest first) when
-    // there is one pass; otherwise warp gw takes tasks gw, gw + nwarps, ...
-    // The gradient sums do not depend on the schedule: each task's share is
-    // summed over its warp in a fixed order and stored at the task's index.
-    const bool dyn = npass == 1 && qctr != nullptr;
+    // Warp tasks come from a work queue per candidate pass (with the lists,
+    // longest first), so the warps of a pass finish together; without a
+    // queue warp gw takes tasks gw, gw + nwarps, ...  A bin's sums never
+    // leave its warp, and the gradient sums do not depend on the schedule
+    // either: each task's share is stored at the task's index.
+    const bool dyn = qctr != nullptr;
     auto take = [&]() -> int {
       unsigned v = 0u;
-      if (lane == 0) v = atomicAdd(qctr, 1u);
+      if (lane == 0) v = atomicAdd(qctr + pass, 1u);
       return (int)__shfl_sync(0xffffffffu, v, 0);
     };
     const int* order = (dyn && lists) ? tl_order : nullptr;
@@ -822,7 +823,7 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   }
   L.partial = o; o = align256(o + sizeof(double) * 5 * npart);
   L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)nh);
-  L.queue = o; o = align256(o + sizeof(unsigned));
+  L.queue = o; o = align256(o + sizeof(unsigned) * (size_t)(n_cand > 0 ? n_cand : 1));
   L.total = o;
   return L;
 }
