@@ -293,10 +293,22 @@ __global__ void __launch_bounds__(kWarps * 32,
             const float gy = fmaf(2.f * (f.a1 - f.a2) + s4, qy, f.a3 * qx);
             d[4] = kTwoPi * (gy * Kx - gx * Ky);
             const float2 mi = make_float2(term.y, -term.x);  // -i * term
+            if (P.norm == 0) {
+              // Eq. 3 as printed needs only the difference A - conj(B): one
+              // signed sum per parameter (wp = 1: the term, wp = 0: minus its
+              // conjugate)
+              const float sg = wp - wm;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-              DPa[j] = cmadd(DPa[j], mi, d[j] * wp);
-              DMa[j] = cmadd(DMa[j], mi, d[j] * wm);
+              for (int j = 0; j < 5; ++j) {
+                DPa[j].x = fmaf(sg * d[j], mi.x, DPa[j].x);
+                DPa[j].y = fmaf(d[j], mi.y, DPa[j].y);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 5; ++j) {
+                DPa[j] = cmadd(DPa[j], mi, d[j] * wp);
+                DMa[j] = cmadd(DMa[j], mi, d[j] * wm);
+              }
             }
           }
         }
