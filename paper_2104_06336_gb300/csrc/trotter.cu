@@ -645,7 +645,7 @@ __global__ void k_variance_final_batched(const __grid_constant__ BatchParams B,
   if (threadIdx.x == 0) var[c] = red[0] / (NR * NR);
 }
 
-// Fixed-order sum of per-block partials (deterministic).
+// Fixed-order sum of nblk rows of nv doubles (one block; deterministic).
 __global__ void k_reduce_partials(const double* partial, int nblk, int nv, double* out) {
   __shared__ double red[256];
   for (int j = 0; j < nv; ++j) {
@@ -794,7 +794,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int kNcFwd = 4;
 constexpr int kNcFwdWide = 8;
 
-constexpr int kMaxTrotBlocks = 2048;  // capacity of the per-block partial sums
+constexpr int kMaxTrotBlocks = 2048;  // largest trotter grid
 
 // One full wave of the persistent grid: SMs x resident blocks per SM (from the
 // occupancy calculator), never more blocks than warp tasks need.
@@ -826,9 +826,9 @@ Layout layout(const eer4d_plan* p, int n_cand, int mode) {
   L.gscale = o; o = align256(o + 2 * sizeof(double));
   const int nh = (mode == TROT_GRAD || mode == TROT_COUNT) ? 0 : n_cand;
   L.H = o; o = align256(o + sizeof(float2) * (size_t)nh * p->g.scan_ny * p->nkx);
-  // per-block partial sums, or in the gradient modes one share per (warp
-  // task, lane) followed by the first-stage sums of the final reduction
-  size_t npart = kMaxTrotBlocks;
+  // the gradient modes: one share per (warp task, lane), then the
+  // first-stage sums of the final reduction
+  size_t npart = 0;
   if (mode == TROT_GRAD || mode == TROT_VARGRAD) {
     const size_t ntask = (size_t)p->nkx * ((p->g.scan_ny + 31) / 32);
     npart = ntask * 32 + kRedBlocks;
