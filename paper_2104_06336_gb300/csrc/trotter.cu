@@ -478,6 +478,11 @@ struct SetDesc {
   float kpm_x, kpm_y;
   int task0;
   float NR;
+  // the dataset plan's membership lists (scan rotation 0), or tl_n = nullptr
+  const uint32_t* tl_bits;
+  const uint32_t* tl_qp;
+  const int* tl_n;
+  int tl_cap;
 };
 
 struct BatchParams {
@@ -508,7 +513,8 @@ __global__ void k_gbar_batched(const __grid_constant__ BatchParams B, const int3
 __global__ void __launch_bounds__(kWarps * 32, 3)
     k_trotter_batched(const __grid_constant__ BatchParams B, const int32_t* __restrict__ bfp,
                       const short2* __restrict__ pix, const CandCoef* __restrict__ coef,
-                      const float2* __restrict__ ek, const double* __restrict__ gscale) {
+                      const float2* __restrict__ ek, const double* __restrict__ gscale,
+                      unsigned* qctr) {
   extern __shared__ unsigned char smem_raw[];
   float2* skk = reinterpret_cast<float2*>(smem_raw);  // [P_bf] (kx, ky)
   int* sp = reinterpret_cast<int*>(skk + B.P_bf);     // [P_bf] kept-pixel index
@@ -519,11 +525,16 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
     sp[q] = p;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * kWarps + warp;
-  const int nwarps = gridDim.x * kWarps;
+  const int lane = threadIdx.x & 31;
+  // warp tasks from a work queue (list lengths differ between tasks); the
+  // numbers a warp takes only grow, so the dataset index only moves forward
+  auto take = [&]() -> int {
+    unsigned v = 0u;
+    if (lane == 0) v = atomicAdd(qctr, 1u);
+    return (int)__shfl_sync(0xffffffffu, v, 0);
+  };
   int si = 0;
-  for (int t = gw; t < B.ntask; t += nwarps) {
+  for (int t = take(); t < B.ntask; t = take()) {
     while (si + 1 < B.n_sets && t >= B.s[si + 1].task0) ++si;  // tasks only grow
     const SetDesc& D = B.s[si];
     const CandCoef cf = coef[si];
@@ -558,7 +569,56 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
       SP = cmadd(SP, term, wp);
       SM = cmadd(SM, term, wm);
     };
-    for (int q0 = 0; q0 < B.P_bf; q0 += kBatch) {
+    // at scan rotation 0 the dataset's membership lists give each lane its
+    // members in ascending q, the order of the loop below: the same terms
+    // in the same order, without the set tests
+    const bool lists = D.tl_n != nullptr && cf.c == 1.f && cf.s == 0.f;
+    if (lists) {
+      int n = D.tl_n[tl];
+      if (n < 0 || n > D.tl_cap) n = 0;
+      const uint32_t* bits = D.tl_bits + (size_t)tl * (D.tl_cap / 32) * 64;
+      const uint32_t* qps = D.tl_qp + (size_t)tl * D.tl_cap;
+      for (int e0 = 0; e0 < n; e0 += 32) {
+        const uint32_t wP = __ldg(bits + 2 * e0 + lane);
+        const uint32_t wM = __ldg(bits + 2 * e0 + 32 + lane);
+        const uint32_t ql = __ldg(qps + e0 + lane);
+        const int m = n - e0 < 32 ? n - e0 : 32;
+        for (int s0 = 0; s0 < m; s0 += kBatch) {
+          uint32_t xv[kBatch];
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) xv[i] = __shfl_sync(0xffffffffu, ql, s0 + i);
+          const unsigned mP = (wP >> s0) & 0xffu, mM = (wM >> s0) & 0xffu;
+          nP += __popc(mP);
+          nM += __popc(mM);
+          const unsigned mAny = mP | mM;
+          if (mAny == 0u) continue;
+          float2 gb[kBatch];
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const int prow = (int)(xv[i] & 0xffffu);
+            gb[i] = ((mAny >> i) & 1u) && prow < B.P_pad ? Gl[(size_t)prow * D.Ny]
+                                                          : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < kBatch; ++i) {
+            const bool memP = (mP >> i) & 1u, memM = (mM >> i) & 1u;
+            if (!(memP || memM)) continue;
+            int q = (int)(xv[i] >> 16);
+            if (q >= B.P_bf) q = 0;  // a bad entry: its G is 0, so its term is 0
+            const float2 kk = skk[q];
+            const float2 g = gb[i];
+            if (!nyq_warp) {
+              const float2 gg = memM ? make_float2(g.x, -g.y) : g;
+              contrib(gg, memM ? Kmx : Kpx, memM ? Kmy : Kpy, kk, q, memM ? 0.f : 1.f);
+            } else {
+              if (memP) contrib(g, Kpx, Kpy, kk, q, 1.f);
+              if (memM) contrib(make_float2(g.x, -g.y), Kmx, Kmy, kk, q, 0.f);
+            }
+          }
+        }
+      }
+    }
+    for (int q0 = 0; q0 < (lists ? 0 : B.P_bf); q0 += kBatch) {
       unsigned mP = 0u, mM = 0u;
 #pragma unroll
       for (int i = 0; i < kBatch; ++i) {
@@ -1049,7 +1109,7 @@ cudaError_t launch_image_from_spectrum(const eer4d_plan* p, const float2* H_in, 
 
 namespace {
 struct BatchedLayout {
-  size_t coef, ek, gscale, vpart, H[kMaxSets], total;
+  size_t coef, ek, gscale, vpart, queue, H[kMaxSets], total;
 };
 BatchedLayout batched_layout(const eer4d_plan* const* plans, int n) {
   BatchedLayout L;
@@ -1059,6 +1119,7 @@ BatchedLayout batched_layout(const eer4d_plan* const* plans, int n) {
   L.ek = o; o = align256(o + sizeof(float2) * (size_t)n * p0->P_pad);
   L.gscale = o; o = align256(o + 2 * sizeof(double) * n);
   L.vpart = o; o = align256(o + sizeof(double) * kVarBlocks * (size_t)n);
+  L.queue = o; o = align256(o + sizeof(unsigned) * (size_t)n);
   for (int i = 0; i < n; ++i) {
     L.H[i] = o;
     o = align256(o + sizeof(float2) * (size_t)plans[i]->g.scan_ny * plans[i]->nkx);
@@ -1082,6 +1143,7 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
   float2* ek = reinterpret_cast<float2*>(sb + L.ek);
   double* gsc = reinterpret_cast<double*>(sb + L.gscale);
   double* vpart = reinterpret_cast<double*>(sb + L.vpart);
+  unsigned* qctr = reinterpret_cast<unsigned*>(sb + L.queue);
   BatchParams B;
   B.n_sets = n;
   B.P_pad = p0->P_pad;
@@ -1105,13 +1167,17 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
     D.kpm_y = (float)p->g.kpm_y;
     D.task0 = ntask;
     D.NR = (float)p->F;
+    D.tl_bits = p->d_tl_bits;
+    D.tl_qp = p->d_tl_qp;
+    D.tl_n = p->d_tl_n;
+    D.tl_cap = p->tl_cap;
     ntask += p->nkx * ((D.Ny + 31) / 32);
   }
   B.ntask = ntask;
   cudaError_t e;
   stage_begin(p0, EER4D_STAGE_TROTTER, s);
   k_prep<<<n, 256, 0, s>>>(aberr, n, p0->d_pix, p0->P_pad, p0->P, p0->g.dalpha_rad, p0->g.lambda_A,
-                           coef, ek, st, 1);
+                           coef, ek, st, 1, qctr);
   k_gbar_batched<<<n, 256, 0, s>>>(B, p0->d_bfp, gsc);
   count_launches(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1126,7 +1192,7 @@ cudaError_t launch_trotter_batched(const eer4d_plan* const* plans, const float2*
   const int need = (ntask + kWarps - 1) / kWarps;
   if (nblk > need) nblk = need;
   if (nblk < 1) nblk = 1;
-  k_trotter_batched<<<nblk, kWarps * 32, sm, s>>>(B, p0->d_bfp, p0->d_pix, coef, ek, gsc);
+  k_trotter_batched<<<nblk, kWarps * 32, sm, s>>>(B, p0->d_bfp, p0->d_pix, coef, ek, gsc, qctr);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   stage_end(p0, EER4D_STAGE_TROTTER, s);
